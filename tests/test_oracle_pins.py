@@ -1,0 +1,372 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each test checks the oracle against something the paper or mathematics fixes:
+textbook MAX-CUT values, an independent library implementation of Philox,
+numpy linear algebra for the quadratic forms, closed forms of the schedule,
+the p-bit's defining probability (1 + tanh x)/2 (Eq. 1), and limit cases.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_14476_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _dense_w(g):
+    W = np.zeros((g.n, g.n), np.int64)
+    W[g.src, g.dst] = g.w
+    W[g.dst, g.src] = g.w
+    return W
+
+
+def _small_graph(n, m, seed, kind="pm1"):
+    return inputs.erdos_renyi_gnm(n, m, seed, kind)
+
+
+# ---------------------------------------------------------------- Philox ----
+
+def test_philox_matches_triton_interpreter():
+    """Philox4x32-10 equals Triton's independent implementation (CPU interpreter)."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    cases = [([0, 0, 0, 0], [0, 0]), ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2)]
+    for _ in range(30):
+        cases.append((rng.integers(0, 2**32, 4, dtype=np.uint64).tolist(),
+                      rng.integers(0, 2**32, 2, dtype=np.uint64).tolist()))
+    script = os.path.join(ROOT, "tests", "golden", "triton_philox.py")
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    res = subprocess.run([sys.executable, script], input=json.dumps(cases), capture_output=True, text=True,
+                         env=env, timeout=600)
+    if res.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {res.stderr[-300:]}")
+    ref = json.loads(res.stdout)
+    for (ctr, key), want in zip(cases, ref):
+        got = oracle.philox4x32_10(ctr, key).tolist()
+        assert got == want, (ctr, key, got, want)
+
+
+def test_draw_grids():
+    """r lies on the odd 2^24 midpoint grid of (-1,1); u on the 2^24 grid of [0,1)."""
+    rs, us = [], []
+    for node in range(64):
+        for trial in range(8):
+            r, u = oracle.draw_ru(123, 4, node, 9, trial)
+            rs.append(r)
+            us.append(u)
+    rs, us = np.array(rs), np.array(us)
+    assert np.all(np.abs(rs) < 1.0)
+    k = rs * 2**24
+    assert np.all(k == np.round(k)) and np.all(np.round(k).astype(np.int64) % 2 == 1)
+    q = us * 2**24
+    assert np.all(q == np.round(q)) and np.all((us >= 0) & (us < 1))
+    assert abs(np.corrcoef(rs, us)[0, 1]) < 0.15
+
+
+# ------------------------------------------------------------- MAX-CUT ------
+
+@pytest.mark.parametrize("n", [3, 4, 7, 10])
+def test_bruteforce_complete_graph(n):
+    """Max cut of K_n with unit weights is floor(n/2)*ceil(n/2)."""
+    i, j = np.triu_indices(n, 1)
+    val, _ = oracle.bruteforce_maxcut(n, i, j, np.ones(len(i), np.int8))
+    assert val == (n // 2) * ((n + 1) // 2)
+
+
+@pytest.mark.parametrize("n", [5, 6, 11, 12])
+def test_bruteforce_cycles(n):
+    """Even cycle: every edge cut; odd cycle: all but one."""
+    i = np.arange(n)
+    j = (i + 1) % n
+    val, _ = oracle.bruteforce_maxcut(n, np.minimum(i, j), np.maximum(i, j), np.ones(n, np.int8))
+    assert val == (n if n % 2 == 0 else n - 1)
+
+
+def test_bruteforce_bipartite_and_negative():
+    """Complete bipartite K_{3,4}: all 12 edges; all-negative weights: empty cut."""
+    a, b = np.meshgrid(np.arange(3), np.arange(3, 7), indexing="ij")
+    val, best = oracle.bruteforce_maxcut(7, a.ravel(), b.ravel(), np.ones(12, np.int8))
+    assert val == 12
+    assert len(set(best[:3])) == 1 and len(set(best[3:])) == 1 and best[0] != best[3]
+    i, j = np.triu_indices(6, 1)
+    val, _ = oracle.bruteforce_maxcut(6, i, j, -np.ones(len(i), np.int8))
+    assert val == 0
+
+
+def test_bruteforce_maximiser_attains_value():
+    g = _small_graph(14, 40, 3)
+    val, best = oracle.bruteforce_maxcut(g.n, g.src, g.dst, g.w)
+    assert oracle.cut(g.src, g.dst, g.w, best[:, None])[0] == val
+    # no single flip improves the optimum
+    for i in range(g.n):
+        s = best.copy()
+        s[i] = -s[i]
+        assert oracle.cut(g.src, g.dst, g.w, s[:, None])[0] <= val
+
+
+def test_cut_quadratic_identity_both_orientations():
+    """cut = (sum_ij w_ij - sum_ij w_ij s_i s_j)/4 (dense numpy), and cut(s) = cut(-s)."""
+    g = _small_graph(60, 400, 5)
+    W = _dense_w(g)
+    s = inputs.random_spins(g.n, 33, 9)
+    c = oracle.cut(g.src, g.dst, g.w, s)
+    quad = np.einsum("it,ij,jt->t", s.astype(np.int64), W, s.astype(np.int64))
+    assert np.array_equal(4 * c, W.sum() - quad)
+    assert np.array_equal(c, oracle.cut(g.src, g.dst, g.w, -s))
+
+
+def test_cut_equals_w_minus_h_over_two():
+    """With h = 0 and J = -w: cut = (W - H)/2 (Eq. 2 against the MAX-CUT objective)."""
+    g = _small_graph(80, 600, 11)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, 17, 2)
+    H = oracle.energy(csr, s)
+    c = oracle.cut(g.src, g.dst, g.w, s)
+    assert np.array_equal(2 * c, int(g.w.astype(np.int64).sum()) - H)
+
+
+def test_energy_with_bias_matches_quadratic_form():
+    """H = -h.s - 1/2 s^T J s with J = -w, via numpy."""
+    g = _small_graph(50, 300, 13)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    h = np.random.default_rng(1).integers(-5, 6, g.n).astype(np.int32)
+    s = inputs.random_spins(g.n, 9, 4)
+    J = -_dense_w(g)
+    si = s.astype(np.int64)
+    want = -(h.astype(np.int64) @ si) - np.einsum("it,ij,jt->t", si, J, si) // 2
+    assert np.array_equal(oracle.energy(csr, s, h), want)
+
+
+def test_fields_equal_dense_matmul():
+    """D = h + J s equals an int64 dense matmul, with J = -w symmetric."""
+    g = _small_graph(70, 700, 17)
+    g.w = (np.random.default_rng(3).integers(-127, 128, g.m)).astype(np.int8)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    h = np.random.default_rng(2).integers(-50, 50, g.n).astype(np.int32)
+    s = inputs.random_spins(g.n, 21, 8)
+    J = -_dense_w(g)
+    assert np.array_equal(J, J.T)
+    want = h[:, None].astype(np.int64) + J @ s.astype(np.int64)
+    assert np.array_equal(oracle.fields(csr, s, h), want)
+
+
+def test_csr_rejects_invalid_edges():
+    with pytest.raises(ValueError):
+        oracle.Csr(4, [0], [0], [1])            # self loop
+    with pytest.raises(ValueError):
+        oracle.Csr(4, [0, 1], [1, 0], [1, 1])   # duplicate undirected edge
+    with pytest.raises(ValueError):
+        oracle.Csr(4, [0], [4], [1])            # out of range
+    with pytest.raises(ValueError):
+        oracle.Csr(4, [0], [1], [-128])         # J = -w overflows int8
+
+
+# ------------------------------------------------------------ schedule ------
+
+def test_mean_s_closed_forms():
+    """K_n with w=+1: s_i = (n-1)/n exactly; general rows: numpy population variance."""
+    n = 40
+    i, j = np.triu_indices(n, 1)
+    csr = oracle.Csr(n, i, j, np.ones(len(i), np.int8))
+    assert oracle.mean_s(csr) == pytest.approx((n - 1) / n, rel=1e-13)
+    g = _small_graph(90, 700, 21)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    J = -_dense_w(g).astype(np.float64)
+    want = np.mean(np.sqrt((g.n - 1) * np.var(J, axis=1)))
+    assert oracle.mean_s(csr) == pytest.approx(want, rel=1e-12)
+
+
+def test_i0_table_closed_form():
+    """I0(t) = I0min (I0max/I0min)^(t/(S-1)); first entry exact, last within S ulps."""
+    for (lo, hi, S) in [(0.1, 10.0, 1000), (0.05, 5.0, 2000), (0.013, 1.7, 7)]:
+        tab = oracle.i0_table(lo, hi, S)
+        assert tab.dtype == np.float32 and len(tab) == S
+        assert tab[0] == np.float32(lo)
+        t = np.arange(S)
+        want = lo * (hi / lo) ** (t / (S - 1))
+        assert np.allclose(tab, want, rtol=4e-7 + S * 2.3e-16)
+        assert np.all(np.diff(tab) > 0)
+    assert np.array_equal(oracle.i0_table(0.5, 9.0, 1), np.array([0.5], np.float32))
+
+
+def test_schedule_normalisation():
+    g = _small_graph(50, 200, 2, "+1")
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    ms = oracle.mean_s(csr)
+    tab = oracle.schedule(csr, 0.1, 10.0, 100)
+    assert tab[0] == np.float32(0.1 / ms)
+    assert tab[-1] == pytest.approx(10.0 / ms, rel=1e-6)
+    assert np.array_equal(oracle.schedule(csr, 0.1, 10.0, 100, normalize=False), oracle.i0_table(0.1, 10.0, 100))
+
+
+# --------------------------------------------------------- update rule ------
+
+def _star(n_leaves, w=1):
+    """Node 0 joined to n_leaves leaves (weights w)."""
+    src = np.zeros(n_leaves, np.int32)
+    dst = np.arange(1, n_leaves + 1, dtype=np.int32)
+    return n_leaves + 1, src, dst, np.full(n_leaves, w, np.int8)
+
+
+def test_zero_temperature_is_fair_coin():
+    """I0 = 0: each decision is +1 with probability exactly 1/2 (Eq. 1 at I = 0)."""
+    g = _small_graph(64, 300, 4)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, 512, 1)
+    ups = 0
+    for step in range(4):
+        ups += int((oracle.step(csr, s, step, 0.0, seed=99) == 1).sum())
+    total = 4 * g.n * 512
+    assert abs(ups / total - 0.5) < 5 * 0.5 / np.sqrt(total)
+
+
+def test_pbit_probability_is_one_plus_tanh_over_two():
+    """P(+1) = (1 + tanh(x))/2 for fixed x: Eq. 1 with r uniform on (-1, 1)."""
+    n, src, dst, w = _star(3, w=-1)              # J = +1 for every leaf edge
+    csr = oracle.Csr(n, src, dst, w)
+    T = 4096
+    s = np.ones((n, T), np.int8)                  # all up: field on the hub D = 3
+    for I0, lam, delta in [(0.2, 1.0, 0.0), (0.05, 1.3, -0.4), (0.5, 0.7, 0.9)]:
+        var = {"intensity": np.full(n, lam, np.float32), "offset": np.full(n, delta, np.float32),
+               "p_update": np.ones(n, np.float32)}
+        x = I0 * (np.float32(lam) * 3.0 + np.float32(delta))
+        hits, tot = 0, 0
+        for step in range(6):
+            out = oracle.step(csr, s, step, I0, seed=5, variability=var)
+            hits += int((out[0] == 1).sum())
+            tot += T
+        p = (1 + np.tanh(x)) / 2
+        assert abs(hits / tot - p) < 5 * np.sqrt(p * (1 - p) / tot), (I0, lam, delta)
+
+
+def test_offset_modes_recover_x():
+    """x from (gap + r): North-star I0(l D + d), listing l I0 (D + d), equation l (I0 D + d)."""
+    n, src, dst, w = _star(5, w=-1)
+    csr = oracle.Csr(n, src, dst, w)
+    T = 8
+    s = np.ones((n, T), np.int8)
+    s[2] = -1                                     # hub field D = 5 - 2 = 3
+    lam = np.float32(1.7)
+    dl = np.float32(0.3)
+    var = {"intensity": np.full(n, lam, np.float32), "offset": np.full(n, dl, np.float32)}
+    I0 = np.float32(0.11)
+    lam64, dl64, I064 = float(lam), float(dl), float(I0)
+    want = {oracle.OFFSET_NORTHSTAR: I064 * (lam64 * 3 + dl64),
+            oracle.OFFSET_LISTING: lam64 * I064 * (3 + dl64),
+            oracle.OFFSET_EQUATION: lam64 * (I064 * 3 + dl64)}
+    for mode, x in want.items():
+        _, gap = oracle.step(csr, s, 3, I0, seed=8, variability=var, offset_mode=mode, want_gap=True)
+        for t in range(T):
+            r, _ = oracle.draw_ru(8, 0, 0, 3, t)
+            assert np.arctanh(gap[0, t] + r) == pytest.approx(x, rel=1e-9)
+
+
+def test_modes_coincide_without_variability():
+    g = _small_graph(40, 150, 6)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, 16, 3)
+    outs = [oracle.step(csr, s, 2, 0.37, seed=1, offset_mode=m) for m in range(3)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_infinite_temperature_limit_is_sign_of_field():
+    """I0 -> inf: new state = sgn(D) wherever D != 0, since |r| < 1 and tanh -> +-1."""
+    g = _small_graph(60, 500, 8)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, 40, 6)
+    D = oracle.fields(csr, s)
+    out = oracle.step(csr, s, 0, 1e30, seed=3)
+    nz = D != 0
+    assert np.array_equal(out[nz], np.sign(D[nz]).astype(np.int8))
+    # D == 0: a fair coin again
+    assert 0.3 < (out[~nz] == 1).mean() < 0.7
+
+
+def test_single_node_greedy_never_lowers_cut():
+    """J = -w: a node aligning with its field (I0 -> inf) never lowers the cut."""
+    g = _small_graph(50, 300, 12)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, 64, 7)
+    before = oracle.cut(g.src, g.dst, g.w, s)
+    for k in range(0, g.n, 7):
+        p = np.zeros(g.n, np.float32)
+        p[k] = 1.0
+        out = oracle.step(csr, s, 1, 1e30, seed=2, variability={"p_update": p})
+        assert np.all(oracle.cut(g.src, g.dst, g.w, out) >= before)
+        assert np.array_equal(np.delete(out, k, 0), np.delete(s, k, 0))
+
+
+def test_update_probability_and_hold():
+    """p = 0 holds every node; otherwise the updated fraction is p (binomial)."""
+    g = _small_graph(64, 300, 9)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, 256, 5)
+    held = oracle.step(csr, s, 0, 1.0, seed=4, variability={"p_update": np.zeros(g.n, np.float32)})
+    assert np.array_equal(held, s)
+    # at I0 -> inf a node that updates takes sgn(D); count nodes whose new state differs from the old
+    # and sgn(D): those must be held.  Fraction of "updated" = p in expectation.
+    p = 0.3
+    D = oracle.fields(csr, s)
+    out = oracle.step(csr, s, 0, 1e30, seed=4, variability={"p_update": np.full(g.n, p, np.float32)})
+    nz = (D != 0) & (np.sign(D) != s)
+    moved = (out[nz] != s[nz]).mean()
+    tot = nz.sum()
+    assert abs(moved - p) < 5 * np.sqrt(p * (1 - p) / tot)
+
+
+def test_init_spins_balanced():
+    s = oracle.init_spins(500, 64, seed=77)
+    assert set(np.unique(s)) == {-1, 1}
+    assert abs(s.mean()) < 5 / np.sqrt(s.size)
+    assert not np.array_equal(s, oracle.init_spins(500, 64, seed=78))
+
+
+def test_anneal_with_timing_variability_finds_bruteforce_optimum():
+    """With timing variability (p = 0.7) pSA reaches the exact maximum cut in most trials.
+
+    The Discussion attributes pSA's gain under timing variability to the
+    de-synchronised updates; fully synchronous pSA is trapped instead (next test).
+    """
+    g = _small_graph(16, 40, 31, "+1")
+    best, _ = oracle.bruteforce_maxcut(g.n, g.src, g.dst, g.w)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    T = 64
+    tab = oracle.schedule(csr, 0.1, 10.0, 400)
+    s0 = oracle.init_spins(g.n, T, seed=3)
+    var = {"p_update": np.full(g.n, 0.7, np.float32)}
+    cuts = oracle.cut(g.src, g.dst, g.w, oracle.anneal(csr, s0, tab, seed=3, variability=var))
+    assert cuts.max() == best
+    assert (cuts == best).mean() > 0.5
+    # the synchronous run on the same seeds ends far below
+    sync = oracle.cut(g.src, g.dst, g.w, oracle.anneal(csr, s0, tab, seed=3))
+    assert sync.mean() < 0.5 * cuts.mean()
+
+
+def test_synchronous_two_cycle_at_low_temperature():
+    """Ideal synchronous pSA oscillates: all +1 -> all -1 -> all +1 at large I0 (w = +1)."""
+    g = _small_graph(30, 80, 4, "+1")
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n)
+    assert deg.min() > 0
+    s = np.ones((g.n, 16), np.int8)
+    a = oracle.step(csr, s, 0, 1e30, seed=1)
+    b = oracle.step(csr, a, 1, 1e30, seed=1)
+    assert np.all(a == -1) and np.all(b == 1)
+
+
+def test_anneal_resume_identity():
+    """Steps [0,S) equal steps [0,k) followed by [k,S) (stateless counter RNG)."""
+    g = _small_graph(30, 90, 2)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, 0.1, 10.0, 50)
+    s0 = oracle.init_spins(g.n, 8, seed=1)
+    full = oracle.anneal(csr, s0, tab, seed=1)
+    half = oracle.anneal(csr, s0, tab, seed=1, step_end=20)
+    rest = oracle.anneal(csr, half, tab, seed=1, step_begin=20)
+    assert np.array_equal(full, rest)
