@@ -1,0 +1,299 @@
+"""Benchmark: spin-updates/s of the p-bit annealing hot path on GB300.
+
+One "step" of this benchmark is one complete anneal of the workload (every
+schedule step of every trial) followed by the exact per-trial cut, on inputs
+already resident in HBM.  The default workload is the dense one: K_2000 with
+w in {-1,+1}, 256 trials, 2000 steps, I0 0.05->5, variability on
+(intensity ~ N(1, 0.1^2), offset ~ N(0, 0.1^2), update probability
+~ clip(N(0.9, 0.05^2), 0, 1)).  Other workloads: --config sparse (100x200
+torus, 1024 trials, 5000 steps), plain (G(800,19176), 16 trials, 1000 steps,
+ideal p-bits).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle as
+the reference arm on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_14476_gb300 import inputs  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload(name: str):
+    if name == "dense":
+        return inputs.dense_k2000()
+    if name == "sparse":
+        return inputs.sparse_torus20000()
+    if name == "plain":
+        return inputs.plain_er800()
+    raise SystemExit(f"unknown config {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "measured"}
+    except Exception:  # noqa: BLE001
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+                "source": "fallback"}
+
+
+# ----------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        busy = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle ----
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """Time the oracle (single-threaded FP64) on a bounded sample: all trials, first k schedule steps."""
+    import oracle
+    g = w.graph
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
+    s0 = oracle.init_spins(g.n, w.trials, w.seed, w.instance)
+    t0 = time.perf_counter()
+    oracle.anneal(csr, s0, tab, w.seed, w.instance, variability=w.var, step_end=1)
+    one = max(time.perf_counter() - t0, 1e-6)
+    k = int(max(1, min(w.steps, budget_s / one)))
+    t0 = time.perf_counter()
+    oracle.anneal(csr, s0, tab, w.seed, w.instance, variability=w.var, step_end=k)
+    dt = time.perf_counter() - t0
+    upd = g.n * w.trials * k
+    return {"value": upd / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{w.name}: all {w.trials} trials, schedule steps [0,{k}) of {w.steps} "
+                      f"({upd:.3g} updates, {dt:.1f} s)"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t_all = []
+    base = None
+    for it in range(args.warmup + args.steps):
+        b = cpu_baseline(w, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if it >= args.warmup:
+            t_all.append(b["value"])
+            base = b
+    val = float(np.mean(t_all))
+    upd_run = w.graph.n * w.trials * w.steps
+    line = {"impl": "reference", "metric": "spin-updates/s", "value": val, "unit": "spin-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * upd_run / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": w.name},
+            "cpu_baseline": {**base, "value": val},
+            "e2e": {"value": val, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main ----
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "sparse", "dense", "resident"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = workload(args.config)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    from paper_2601_14476_gb300 import pbit
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # each rank anneals its own instance of the workload (weak scaling, no data-path collective)
+    w.instance = rank
+    kernel = {"auto": pbit.KERNEL_AUTO, "sparse": pbit.KERNEL_SPARSE, "dense": pbit.KERNEL_DENSE,
+              "resident": pbit.KERNEL_RESIDENT}[args.kernel]
+    g = w.graph
+    G = pbit.Graph.from_inputs(g, dense=(args.config == "dense"))
+    T, S = w.trials, w.steps
+    stream = torch.cuda.current_stream()
+    spins = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+    cuts = torch.empty(T, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    params, keep = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
+                                    kernel=kernel, variability=w.var, stream=stream)
+
+    def one_run():
+        pbit.pbit_anneal(G.handle, params, None, spins)
+        pbit.pbit_cut_device(G.handle, spins, T, cuts, stream)
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = pbit.pbit_launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()                     # L2 flushed between timed steps (not timed)
+            a.record(stream)
+            one_run()
+            b.record(stream)
+        torch.cuda.synchronize()
+    launches = pbit.pbit_launch_count() - launches0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = float(np.mean(ms))
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    upd_run = g.n * T * S
+    value = world * upd_run / (ms_step * 1e-3)
+
+    # dominant kernel: the step loop; average launch duration from events around the anneal alone
+    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = pbit.pbit_launch_count()
+    ka.record(stream)
+    pbit.pbit_anneal(G.handle, params, None, spins)
+    kb.record(stream)
+    torch.cuda.synchronize()
+    anneal_launches = pbit.pbit_launch_count() - l0 - 1   # minus the initial-state kernel
+    anneal_ms = ka.elapsed_time(kb)
+    pk = peaks()
+    info = G.info()
+    mean_deg = 2.0 * g.m / g.n
+    per_launch_ms = anneal_ms / max(1, anneal_launches)
+    steps_per_launch = S / max(1, anneal_launches)
+    # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
+    alg_bytes = g.n * T * (mean_deg + 2.0) * steps_per_launch
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "kernel": "sparse_step_kernel", "peak_source": pk["source"]}
+
+    # end to end through the C ABI from host buffers: graph upload, anneal, cut to host
+    e2e_ms = []
+    h2d = g.m * (4 + 4 + 1) + (3 * g.n * 4 if w.var else 0) + S * 4
+    d2h = T * 8
+    for it in range(2 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = pbit.Graph.from_inputs(g, dense=(args.config == "dense"))
+        out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+        p2, keep2 = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
+                                     kernel=kernel, variability=w.var, stream=stream)
+        pbit.pbit_anneal(G2.handle, p2, None, out)
+        host_cuts = pbit.pbit_cut(G2.handle, out, T, stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        G2.close()
+        if it >= 2:
+            e2e_ms.append(dt * 1e3)
+    e2e_val = world * upd_run / (np.mean(e2e_ms) * 1e-3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(w)
+    line = {
+        "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": g.n, "edges": g.m, "trials": T, "anneal_steps": S,
+                   "variability": w.var is not None, "l2": "flushed between timed steps",
+                   "kernel": args.kernel, "mean_cut": float(host_cuts.mean()),
+                   "updates_per_step": upd_run},
+        "roofline": roofline,
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_val, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

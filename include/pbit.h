@@ -1,0 +1,210 @@
+/*
+ * pbit.h - C ABI of the GB300 p-bit simulated-annealing library (libpbit.so).
+ *
+ * The library solves MAX-CUT instances by p-bit simulated annealing (pSA)
+ * with the device-variability p-bit of arXiv 2601.14476:
+ *
+ *   Eq. (3) "eqn:conv":  D_i = h_i + sum_j J_ij sigma_j        (exact integer field)
+ *   Eq. (6) "eqn:pbits_variability", in the form
+ *            sigma_i <- +1 if tanh(I0(t) * (lambda_i * D_i + delta_i)) - r > 0, else -1,
+ *            applied only when the node's timing draw u < p_i (otherwise it holds),
+ *            all nodes of a trial updated synchronously;
+ *   Methods "CUDA programming and experimental conditions": I0(t+1) = I0(t)/beta,
+ *            beta = (I0min/I0max)^(1/(S-1)), I0min = c_min/mean(s_i), I0max = c_max/mean(s_i),
+ *            s_i = sqrt((n-1) Var(J_i,:)); MAX-CUT weights w enter as J = -w, h = 0.
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return pbit_status; none aborts.  On failure
+ *    pbit_last_error() returns a thread-local message.
+ *  - Spins are int8 in {-1,+1}, TRIAL-MAJOR: spins[i*T + t] is node i of trial t.
+ *  - "device" pointers are CUDA global memory of the graph's device (e.g. a
+ *    torch tensor's data_ptr()); "host" pointers are ordinary CPU memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Work is enqueued on it in order; entry points that return
+ *    results in host memory synchronise that stream before returning.
+ *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key =
+ *    (seed low word, seed high word) and counter = (node, step, trial/2,
+ *    instance); the even trial of a pair uses output words (0,1), the odd one
+ *    (2,3), as (r, u): r = (2*(w0>>8)+1-2^24)/2^24, u = (w1>>8)/2^24.  The
+ *    initial state (step counter 0xFFFFFFFF) is +1 iff r < 0.  Results are
+ *    therefore a pure function of (graph, parameters, seed, instance) and do
+ *    not depend on the kernel, batch or server slot that computed them.
+ */
+#ifndef PBIT_H
+#define PBIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PBIT_OK = 0,
+    PBIT_PENDING = 1,          /* pbit_server_poll: request not finished yet */
+    PBIT_E_INVALID = -1,       /* bad argument, bad edge list or shape */
+    PBIT_E_NOMEM = -2,         /* host or device allocation failed */
+    PBIT_E_CUDA = -3,          /* a CUDA runtime call failed (message has the text) */
+    PBIT_E_TIMEOUT = -4,       /* a bounded device-side wait ran out; state undefined */
+    PBIT_E_BUDGET = -5,        /* request larger than the server's HBM budget */
+    PBIT_E_UNSUPPORTED = -6,   /* the forced kernel cannot run this shape */
+    PBIT_E_NOTFOUND = -7       /* unknown request id */
+} pbit_status;
+
+/* Thread-local text of the last failure on this thread ("" if none). */
+const char* pbit_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t pbit_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+int64_t pbit_launch_count(void);
+
+/* ------------------------------------------------------------------------ */
+/* Instance (MAX-CUT problem statement, Methods; Eq. 2 "eqn:Ising")          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct pbit_graph_s* pbit_graph;
+
+#define PBIT_GRAPH_DENSE 1u     /* also build the dense tensor-core operand of J */
+
+/*
+ * Create a MAX-CUT instance on the current CUDA device.
+ *   n        number of nodes (1 <= n < 2^31)
+ *   n_edges  number of undirected edges (>= 0)
+ *   src,dst  HOST int32[n_edges] endpoints, 0 <= src,dst < n, src != dst, no
+ *            undirected edge listed twice
+ *   w        HOST int8[n_edges] MAX-CUT weights, -127..127 (J = -w)
+ *   h        HOST int32[n] Ising biases, or NULL for h = 0
+ *   flags    PBIT_GRAPH_DENSE to also build the dense operand (needs |w| <= 16)
+ *   out      receives the handle
+ * The library copies everything it needs (CSR of J in HBM; the caller keeps
+ * ownership of its arrays).  Synchronous.  Errors: PBIT_E_INVALID for a
+ * malformed edge list, PBIT_E_NOMEM, PBIT_E_CUDA.
+ */
+pbit_status pbit_graph_create(int32_t n, int64_t n_edges, const int32_t* src, const int32_t* dst,
+                              const int8_t* w, const int32_t* h, uint32_t flags, pbit_graph* out);
+
+/* Release a graph and its device memory (NULL is ignored). Synchronises the device. */
+void pbit_graph_destroy(pbit_graph g);
+
+typedef struct {
+    int32_t n;             /* nodes */
+    int64_t n_edges;       /* undirected edges */
+    int32_t max_degree;    /* largest row of the CSR */
+    int32_t unit_weights;  /* 1 if every |w| == 1 */
+    int32_t has_dense;     /* 1 if the dense tensor-core operand was built */
+    int32_t device;        /* CUDA device ordinal the graph lives on */
+    double mean_s;         /* mean_i sqrt((n-1) Var(J_i,:)), the schedule's normaliser */
+    int64_t total_weight;  /* W = sum of w over edges (cut = (W - H)/2 when h = 0) */
+    size_t device_bytes;   /* HBM held by the graph */
+} pbit_graph_info_t;
+
+pbit_status pbit_graph_info(pbit_graph g, pbit_graph_info_t* info);
+
+/* ------------------------------------------------------------------------ */
+/* Schedule (Methods: I0(t+1) = I0(t)/beta and the I0min/I0max rule)         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Write the float32 I0 table used by pbit_anneal into HOST float[steps]:
+ * I0(0) = I0min, I0(t+1) = I0(t)/beta in FP64, each entry rounded to float32,
+ * beta = (I0min/I0max)^(1/(steps-1)).  With normalize != 0,
+ * I0min = i0_min/mean_s and I0max = i0_max/mean_s (mean_s from
+ * pbit_graph_info); otherwise the end points are taken as given.
+ * Errors: PBIT_E_INVALID for steps < 1, non-positive end points, or
+ * normalize with mean_s == 0.
+ */
+pbit_status pbit_schedule(pbit_graph g, double i0_min, double i0_max, int32_t normalize, int32_t steps,
+                          float* table);
+
+/* Host-only (no device work): the same float32 table between two absolute
+ * end points, I0(0) = i0_min ... I0(steps-1) ~ i0_max.  Writes HOST float[steps]. */
+pbit_status pbit_i0_table(double i0_min, double i0_max, int32_t steps, float* table);
+
+/* Host-only: validate an edge list like pbit_graph_create and write its
+ * mean_s = mean_i sqrt((n-1) Var(J_i,:)) (population variance over the full
+ * row of length n, zeros included) to *out. */
+pbit_status pbit_mean_s(int32_t n, int64_t n_edges, const int32_t* src, const int32_t* dst, const int8_t* w,
+                        double* out);
+
+/* ------------------------------------------------------------------------ */
+/* Annealing (Eqs. 1, 3, 6; the schedule of the Methods section)             */
+/* ------------------------------------------------------------------------ */
+
+typedef enum {
+    PBIT_OFFSET_NORTHSTAR = 0, /* x = I0 * (lambda*D + delta) */
+    PBIT_OFFSET_LISTING = 1,   /* x = lambda * I0 * (D + delta)   (the paper's pseudo code) */
+    PBIT_OFFSET_EQUATION = 2   /* x = lambda * (I0*D + delta)     (Eq. 6 with Eq. 3) */
+} pbit_offset_mode;
+
+typedef enum {
+    PBIT_KERNEL_AUTO = 0,      /* pick from the graph shape */
+    PBIT_KERNEL_SPARSE = 1,    /* CSR gather kernel, one launch per step */
+    PBIT_KERNEL_DENSE = 2,     /* tensor-core field kernel (needs PBIT_GRAPH_DENSE) */
+    PBIT_KERNEL_RESIDENT = 3   /* whole anneal in one CTA with spins in shared memory */
+} pbit_kernel;
+
+typedef struct {
+    uint32_t struct_size;    /* sizeof(pbit_anneal_params) */
+    int32_t trials;          /* T >= 1 independent trials */
+    int32_t steps;           /* S >= 1 schedule length */
+    int32_t step_begin;      /* first schedule index to run, 0 <= step_begin <= step_end */
+    int32_t step_end;        /* one past the last index to run; 0 means S */
+    double i0_min, i0_max;   /* schedule end points (numerators when i0_normalize) */
+    int32_t i0_normalize;    /* 1: divide the end points by mean_s (the paper's rule) */
+    int32_t offset_mode;     /* pbit_offset_mode */
+    uint64_t seed;           /* Philox key */
+    uint32_t instance;       /* Philox counter word 3 */
+    int32_t kernel;          /* pbit_kernel */
+    const float* intensity;  /* HOST float[n] lambda_i, NULL = 1 */
+    const float* offset;     /* HOST float[n] delta_i, NULL = 0 */
+    const float* p_update;   /* HOST float[n] update probability p_i in [0,1], NULL = 1 */
+    void* stream;            /* cudaStream_t */
+} pbit_anneal_params;
+
+/* Fill `p` with defaults: T=1, S=1, whole schedule, I0 0.1..10 normalised, NORTHSTAR, AUTO. */
+void pbit_anneal_params_default(pbit_anneal_params* p);
+
+/*
+ * Run schedule steps [step_begin, step_end) of a pSA anneal.
+ *   spins_in   DEVICE int8[n*T] start state, or NULL to start from the
+ *              Philox initial state of (seed, instance)
+ *   spins_out  DEVICE int8[n*T] final state; may equal spins_in
+ * Running [0,k) and then [k,S) from its output equals running [0,S).
+ * Stream-ordered on p->stream (this call does not wait for the GPU); it
+ * allocates its scratch with cudaMallocAsync on that stream and copies the
+ * per-node parameters from host memory, so it is not for use under stream
+ * capture.  Errors: PBIT_E_INVALID, PBIT_E_UNSUPPORTED (forced kernel cannot
+ * run the shape), PBIT_E_NOMEM, PBIT_E_CUDA.
+ */
+pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in, int8_t* spins_out);
+
+/* Write the Philox initial state of (seed, instance) to DEVICE int8[n*T]. */
+pbit_status pbit_init_spins(pbit_graph g, int32_t trials, uint64_t seed, uint32_t instance, int8_t* spins,
+                            void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Exact observables (Eq. 3 fields, Eq. 2 energy, the MAX-CUT objective)     */
+/* ------------------------------------------------------------------------ */
+
+/* DEVICE int32[n*T] fields D_i(t) = h_i + sum_j J_ij sigma_j(t). Stream-ordered. */
+pbit_status pbit_fields(pbit_graph g, const int8_t* spins, int32_t trials, int32_t* fields, void* stream);
+
+/*
+ * Per-trial cut = sum over edges of w * [sigma_src != sigma_dst], and energy
+ * H = -sum_i h_i sigma_i - sum_{i<j} J_ij sigma_i sigma_j, exact int64.
+ * `out` is HOST int64[T] (the call synchronises `stream`) when out_on_host
+ * != 0, else DEVICE int64[T] written stream-ordered.
+ */
+pbit_status pbit_cut(pbit_graph g, const int8_t* spins, int32_t trials, int64_t* out, int32_t out_on_host,
+                     void* stream);
+pbit_status pbit_energy(pbit_graph g, const int8_t* spins, int32_t trials, int64_t* out, int32_t out_on_host,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBIT_H */

@@ -1,0 +1,466 @@
+// C-ABI entry points of libpbit.so (declared in include/pbit.h) and the host
+// side of the instance: validation, CSR of J = -w, the I0 schedule, per-node
+// parameters, buffer rotation for the synchronous (Jacobi) step loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pbit_internal.h"
+
+namespace pbit {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+pbit_status fail(pbit_status code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+pbit_status cuda_fail(cudaError_t err, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(err);
+    set_error(m);
+    return err == cudaErrorMemoryAllocation ? PBIT_E_NOMEM : PBIT_E_CUDA;
+}
+
+// --------------------------------------------------------------- schedule ---
+// mean_i sqrt((n-1) Var(J_i,:)) with the population variance over the full
+// row of length n (zeros included), summed in node order in FP64.
+static double compute_mean_s(int32_t n, const std::vector<int32_t>& row_ptr, const std::vector<int8_t>& J) {
+    double acc = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t s1 = 0, s2 = 0;
+        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            s1 += J[k];
+            s2 += (int64_t)J[k] * J[k];
+        }
+        const double mean = (double)s1 / (double)n;
+        double var = (double)s2 / (double)n - mean * mean;
+        if (var < 0.0) var = 0.0;
+        acc += std::sqrt((double)(n - 1) * var);
+    }
+    return acc / (double)n;
+}
+
+pbit_status build_schedule(const Graph& g, double i0_min, double i0_max, int normalize, int steps,
+                           std::vector<float>& out) {
+    if (steps < 1) return fail(PBIT_E_INVALID, "schedule: steps must be >= 1");
+    if (!(i0_min > 0.0) || !(i0_max > 0.0) || !std::isfinite(i0_min) || !std::isfinite(i0_max))
+        return fail(PBIT_E_INVALID, "schedule: I0 end points must be positive and finite");
+    double lo = i0_min, hi = i0_max;
+    if (normalize) {
+        if (!(g.mean_s > 0.0)) return fail(PBIT_E_INVALID, "schedule: mean_s is zero, cannot normalise");
+        lo = i0_min / g.mean_s;
+        hi = i0_max / g.mean_s;
+    }
+    out.resize((size_t)steps);
+    const double beta = steps > 1 ? std::pow(lo / hi, 1.0 / (double)(steps - 1)) : 1.0;
+    double i0 = lo;
+    for (int t = 0; t < steps; ++t) {
+        out[(size_t)t] = (float)i0;
+        i0 = i0 / beta;
+    }
+    return PBIT_OK;
+}
+
+// ---------------------------------------------------------- device memory --
+template <typename T>
+static pbit_status upload(T** dst, const T* src, size_t count, size_t& bytes) {
+    if (count == 0) count = 1;
+    PBIT_CUDA_TRY(cudaMalloc((void**)dst, sizeof(T) * count));
+    if (src) PBIT_CUDA_TRY(cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+    bytes += sizeof(T) * count;
+    return PBIT_OK;
+}
+
+static void release(Graph* g) {
+    if (!g) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    cudaFree(g->row_ptr);
+    cudaFree(g->col);
+    cudaFree(g->J);
+    cudaFree(g->h);
+    cudaFree(g->dense.J_e4m3);
+    cudaSetDevice(cur);
+}
+
+// Per-call device state of one anneal: parameters, schedule and the scratch
+// spin buffer, allocated stream-ordered and freed stream-ordered.
+struct CallBuffers {
+    cudaStream_t s = nullptr;
+    std::vector<void*> blocks;
+    ~CallBuffers() {
+        for (void* p : blocks) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    pbit_status alloc(T** p, size_t count) {
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * count, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+        blocks.push_back((void*)*p);
+        return PBIT_OK;
+    }
+    // copy from (pageable) host memory: CUDA stages the data before the call returns
+    template <typename T>
+    pbit_status put(T** p, const T* host, size_t count) {
+        pbit_status st = alloc(p, count);
+        if (st != PBIT_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(*p, host, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        return PBIT_OK;
+    }
+};
+
+static pbit_status check_device(const Graph* g) {
+    int cur = -1;
+    PBIT_CUDA_TRY(cudaGetDevice(&cur));
+    if (cur != g->device) return fail(PBIT_E_INVALID, "the current CUDA device is not the graph's device");
+    return PBIT_OK;
+}
+
+// Validate the edge list and build the host CSR of J = -w (rows sorted by
+// column), degree and weight statistics and mean_s.  No device work.
+static pbit_status build_host(Graph& g, int32_t n, int64_t n_edges, const int32_t* src, const int32_t* dst,
+                              const int8_t* w, const int32_t* h) {
+    if (n <= 0) return fail(PBIT_E_INVALID, "graph: n must be positive");
+    if (n_edges < 0 || n_edges > (int64_t)0x3FFFFFFF) return fail(PBIT_E_INVALID, "graph: bad edge count");
+    if (n_edges > 0 && (!src || !dst || !w)) return fail(PBIT_E_INVALID, "graph: NULL edge arrays");
+    if (n_edges > (int64_t)n * (n - 1) / 2) return fail(PBIT_E_INVALID, "graph: more edges than node pairs");
+    for (int64_t e = 0; e < n_edges; ++e) {
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+            return fail(PBIT_E_INVALID, "graph: edge endpoint out of range at " + std::to_string(e));
+        if (src[e] == dst[e]) return fail(PBIT_E_INVALID, "graph: self loop at " + std::to_string(e));
+        if (w[e] == -128) return fail(PBIT_E_INVALID, "graph: weight -128 (J = -w overflows int8)");
+    }
+    g.n = n;
+    g.n_edges = n_edges;
+    g.nnz = 2 * n_edges;
+    std::vector<int32_t> deg((size_t)n + 1, 0);
+    for (int64_t e = 0; e < n_edges; ++e) {
+        deg[(size_t)src[e] + 1]++;
+        deg[(size_t)dst[e] + 1]++;
+    }
+    g.h_row_ptr.assign((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) g.h_row_ptr[(size_t)i + 1] = g.h_row_ptr[(size_t)i] + deg[(size_t)i + 1];
+    g.h_col.resize((size_t)std::max<int64_t>(g.nnz, 1));
+    g.h_J.resize((size_t)std::max<int64_t>(g.nnz, 1));
+    std::vector<int32_t> fill(g.h_row_ptr.begin(), g.h_row_ptr.end() - 1);
+    int64_t wsum = 0;
+    g.unit_weights = true;
+    for (int64_t e = 0; e < n_edges; ++e) {
+        const int8_t J = (int8_t)(-w[e]);
+        g.h_col[(size_t)fill[(size_t)src[e]]] = dst[e];
+        g.h_J[(size_t)fill[(size_t)src[e]]++] = J;
+        g.h_col[(size_t)fill[(size_t)dst[e]]] = src[e];
+        g.h_J[(size_t)fill[(size_t)dst[e]]++] = J;
+        wsum += w[e];
+        if (w[e] != 1 && w[e] != -1) g.unit_weights = false;
+    }
+    g.total_weight = wsum;
+    std::vector<std::pair<int32_t, int8_t>> row;
+    int64_t max_field = 0;
+    g.max_degree = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t b = g.h_row_ptr[(size_t)i], e = g.h_row_ptr[(size_t)i + 1];
+        g.max_degree = std::max(g.max_degree, e - b);
+        row.clear();
+        int64_t absum = 0;
+        for (int32_t k = b; k < e; ++k) {
+            row.emplace_back(g.h_col[(size_t)k], g.h_J[(size_t)k]);
+            absum += std::abs((int32_t)g.h_J[(size_t)k]);
+        }
+        std::sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        for (size_t k = 1; k < row.size(); ++k)
+            if (row[k].first == row[k - 1].first)
+                return fail(PBIT_E_INVALID, "graph: duplicate edge (" + std::to_string(i) + "," +
+                                                std::to_string(row[k].first) + ")");
+        for (int32_t k = b; k < e; ++k) {
+            g.h_col[(size_t)k] = row[(size_t)(k - b)].first;
+            g.h_J[(size_t)k] = row[(size_t)(k - b)].second;
+        }
+        const int64_t hi = h ? std::llabs((long long)h[i]) : 0;
+        max_field = std::max(max_field, absum + hi);
+    }
+    if (max_field >= (1 << 24)) return fail(PBIT_E_INVALID, "graph: |field| could reach 2^24");
+    g.max_abs_field = (int32_t)max_field;
+    g.has_h = h != nullptr;
+    if (h) g.h_h.assign(h, h + n);
+    g.mean_s = compute_mean_s(n, g.h_row_ptr, g.h_J);
+    return PBIT_OK;
+}
+
+}  // namespace pbit
+
+using namespace pbit;
+
+struct pbit_graph_s : public Graph {};
+
+extern "C" {
+
+const char* pbit_last_error(void) { return g_last_error.c_str(); }
+
+int32_t pbit_version(void) { return 100; }
+
+int64_t pbit_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pbit_status pbit_graph_create(int32_t n, int64_t n_edges, const int32_t* src, const int32_t* dst, const int8_t* w,
+                              const int32_t* h, uint32_t flags, pbit_graph* out) {
+    if (!out) return fail(PBIT_E_INVALID, "graph_create: out is NULL");
+    *out = nullptr;
+    std::unique_ptr<pbit_graph_s> g(new (std::nothrow) pbit_graph_s());
+    if (!g) return fail(PBIT_E_NOMEM, "graph_create: host allocation");
+    pbit_status st = build_host(*g, n, n_edges, src, dst, w, h);
+    if (st != PBIT_OK) return st;
+    PBIT_CUDA_TRY(cudaGetDevice(&g->device));
+    if ((st = upload(&g->row_ptr, g->h_row_ptr.data(), (size_t)n + 1, g->device_bytes)) != PBIT_OK) goto err;
+    if ((st = upload(&g->col, g->h_col.data(), (size_t)g->nnz, g->device_bytes)) != PBIT_OK) goto err;
+    if ((st = upload(&g->J, g->h_J.data(), (size_t)g->nnz, g->device_bytes)) != PBIT_OK) goto err;
+    if (h && (st = upload(&g->h, h, (size_t)n, g->device_bytes)) != PBIT_OK) goto err;
+    (void)flags;
+    *out = g.release();
+    return PBIT_OK;
+err:
+    release(g.get());
+    return st;
+}
+
+pbit_status pbit_mean_s(int32_t n, int64_t n_edges, const int32_t* src, const int32_t* dst, const int8_t* w,
+                        double* out) {
+    if (!out) return fail(PBIT_E_INVALID, "mean_s: out is NULL");
+    Graph g;
+    pbit_status st = build_host(g, n, n_edges, src, dst, w, nullptr);
+    if (st != PBIT_OK) return st;
+    *out = g.mean_s;
+    return PBIT_OK;
+}
+
+pbit_status pbit_i0_table(double i0_min, double i0_max, int32_t steps, float* table) {
+    if (!table) return fail(PBIT_E_INVALID, "i0_table: table is NULL");
+    Graph g;
+    std::vector<float> tab;
+    pbit_status st = build_schedule(g, i0_min, i0_max, 0, steps, tab);
+    if (st != PBIT_OK) return st;
+    std::memcpy(table, tab.data(), sizeof(float) * tab.size());
+    return PBIT_OK;
+}
+
+void pbit_graph_destroy(pbit_graph g) {
+    if (!g) return;
+    release(g);
+    delete g;
+}
+
+pbit_status pbit_graph_info(pbit_graph g, pbit_graph_info_t* info) {
+    if (!g || !info) return fail(PBIT_E_INVALID, "graph_info: NULL argument");
+    info->n = g->n;
+    info->n_edges = g->n_edges;
+    info->max_degree = g->max_degree;
+    info->unit_weights = g->unit_weights ? 1 : 0;
+    info->has_dense = g->dense.J_e4m3 ? 1 : 0;
+    info->device = g->device;
+    info->mean_s = g->mean_s;
+    info->total_weight = g->total_weight;
+    info->device_bytes = g->device_bytes;
+    return PBIT_OK;
+}
+
+pbit_status pbit_schedule(pbit_graph g, double i0_min, double i0_max, int32_t normalize, int32_t steps,
+                          float* table) {
+    if (!g || !table) return fail(PBIT_E_INVALID, "schedule: NULL argument");
+    std::vector<float> tab;
+    pbit_status st = build_schedule(*g, i0_min, i0_max, normalize, steps, tab);
+    if (st != PBIT_OK) return st;
+    std::memcpy(table, tab.data(), sizeof(float) * tab.size());
+    return PBIT_OK;
+}
+
+void pbit_anneal_params_default(pbit_anneal_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->struct_size = sizeof(pbit_anneal_params);
+    p->trials = 1;
+    p->steps = 1;
+    p->i0_min = 0.1;
+    p->i0_max = 10.0;
+    p->i0_normalize = 1;
+    p->offset_mode = PBIT_OFFSET_NORTHSTAR;
+    p->kernel = PBIT_KERNEL_AUTO;
+}
+
+pbit_status pbit_init_spins(pbit_graph g, int32_t trials, uint64_t seed, uint32_t instance, int8_t* spins,
+                            void* stream) {
+    if (!g || !spins || trials < 1) return fail(PBIT_E_INVALID, "init_spins: bad argument");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    PBIT_CUDA_TRY(launch_init_spins(g->n, trials, seed, instance, spins, (cudaStream_t)stream));
+    return PBIT_OK;
+}
+
+pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in, int8_t* spins_out) {
+    if (!g || !p || !spins_out) return fail(PBIT_E_INVALID, "anneal: NULL argument");
+    if (p->struct_size != sizeof(pbit_anneal_params)) return fail(PBIT_E_INVALID, "anneal: struct_size mismatch");
+    const int32_t T = p->trials, S = p->steps;
+    const int32_t b = p->step_begin, e = p->step_end == 0 ? S : p->step_end;
+    if (T < 1 || S < 1 || b < 0 || e < b || e > S) return fail(PBIT_E_INVALID, "anneal: bad trials/steps range");
+    if ((int64_t)g->n * T > ((int64_t)1 << 40)) return fail(PBIT_E_INVALID, "anneal: n*T too large");
+    if (p->offset_mode < 0 || p->offset_mode > 2) return fail(PBIT_E_INVALID, "anneal: bad offset_mode");
+    if (p->kernel < 0 || p->kernel > 3) return fail(PBIT_E_INVALID, "anneal: bad kernel");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    cudaStream_t s = (cudaStream_t)p->stream;
+    const int64_t cells = (int64_t)g->n * T;
+
+    int kernel = p->kernel;
+    if (kernel == PBIT_KERNEL_DENSE) return fail(PBIT_E_UNSUPPORTED, "anneal: dense kernel not available");
+    if (kernel == PBIT_KERNEL_RESIDENT && !resident_fits(*g, T))
+        return fail(PBIT_E_UNSUPPORTED, "anneal: n*T too large for the shared-memory resident kernel");
+    if (kernel == PBIT_KERNEL_AUTO) kernel = resident_fits(*g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
+
+    // host-side tables
+    std::vector<float> tab;
+    if ((st = build_schedule(*g, p->i0_min, p->i0_max, p->i0_normalize, S, tab)) != PBIT_OK) return st;
+    std::vector<uint32_t> thr;
+    if (p->p_update) {
+        thr.resize((size_t)g->n);
+        for (int32_t i = 0; i < g->n; ++i) {
+            const float pu = p->p_update[i];
+            if (!(pu >= 0.0f && pu <= 1.0f)) return fail(PBIT_E_INVALID, "anneal: p_update outside [0,1]");
+            thr[(size_t)i] = (uint32_t)std::ceil((double)pu * 16777216.0);  // u < p  <=>  (u*2^24) < ceil(p*2^24)
+        }
+    }
+    if (p->intensity)
+        for (int32_t i = 0; i < g->n; ++i)
+            if (!std::isfinite(p->intensity[i])) return fail(PBIT_E_INVALID, "anneal: non-finite intensity");
+    if (p->offset)
+        for (int32_t i = 0; i < g->n; ++i)
+            if (!std::isfinite(p->offset[i])) return fail(PBIT_E_INVALID, "anneal: non-finite offset");
+
+    CallBuffers cb;
+    cb.s = s;
+    StepArgs a{};
+    a.row_ptr = g->row_ptr;
+    a.col = g->col;
+    a.J = g->J;
+    a.h = g->h;
+    a.n = g->n;
+    a.T = T;
+    a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
+    a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.instance = p->instance;
+    a.offset_mode = p->offset_mode;
+    float* d_tab = nullptr;
+    if ((st = cb.put(&d_tab, tab.data(), tab.size())) != PBIT_OK) return st;
+    a.i0_table = d_tab;
+    if (p->intensity) {
+        float* d = nullptr;
+        if ((st = cb.put(&d, p->intensity, (size_t)g->n)) != PBIT_OK) return st;
+        a.par.lambda = d;
+    }
+    if (p->offset) {
+        float* d = nullptr;
+        if ((st = cb.put(&d, p->offset, (size_t)g->n)) != PBIT_OK) return st;
+        a.par.delta = d;
+    }
+    if (p->p_update) {
+        uint32_t* d = nullptr;
+        if ((st = cb.put(&d, thr.data(), thr.size())) != PBIT_OK) return st;
+        a.par.thr = d;
+    }
+    // the start state
+    const int8_t* cur = spins_in;
+    int8_t* init_buf = nullptr;
+    if (!cur) {
+        if (e == b) {
+            init_buf = spins_out;
+        } else if ((st = cb.alloc(&init_buf, (size_t)cells)) != PBIT_OK) {
+            return st;
+        }
+        PBIT_CUDA_TRY(launch_init_spins(g->n, T, p->seed, p->instance, init_buf, s));
+        cur = init_buf;
+    }
+    if (e == b) {
+        if (cur != spins_out)
+            PBIT_CUDA_TRY(cudaMemcpyAsync(spins_out, cur, (size_t)cells, cudaMemcpyDeviceToDevice, s));
+        return PBIT_OK;
+    }
+    if (kernel == PBIT_KERNEL_RESIDENT) {
+        a.in = cur;
+        a.out = spins_out;
+        PBIT_CUDA_TRY(launch_resident_anneal(a, b, e, s));
+        return PBIT_OK;
+    }
+    // Jacobi rotation: step j writes spins_out when (k-1-j) is even, else scratch
+    int8_t* scratch = nullptr;
+    const int32_t k = e - b;
+    if (k >= 2 || cur == spins_out) {
+        if ((st = cb.alloc(&scratch, (size_t)cells)) != PBIT_OK) return st;
+    }
+    if (cur == spins_out && ((k - 1) % 2 == 0)) {
+        // in place with an odd count: the first write would hit the input
+        PBIT_CUDA_TRY(cudaMemcpyAsync(scratch, cur, (size_t)cells, cudaMemcpyDeviceToDevice, s));
+        cur = scratch;
+    }
+    for (int32_t j = 0; j < k; ++j) {
+        int8_t* dst = ((k - 1 - j) % 2 == 0) ? spins_out : scratch;
+        a.step = b + j;
+        a.in = cur;
+        a.out = dst;
+        PBIT_CUDA_TRY(launch_sparse_step(a, s));
+        cur = dst;
+    }
+    return PBIT_OK;
+}
+
+pbit_status pbit_fields(pbit_graph g, const int8_t* spins, int32_t trials, int32_t* fields, void* stream) {
+    if (!g || !spins || !fields || trials < 1) return fail(PBIT_E_INVALID, "fields: bad argument");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    PBIT_CUDA_TRY(launch_fields(*g, spins, trials, fields, (cudaStream_t)stream));
+    return PBIT_OK;
+}
+
+static pbit_status cut_or_energy(pbit_graph g, const int8_t* spins, int32_t trials, int64_t* out, int32_t on_host,
+                                 void* stream, bool energy) {
+    if (!g || !spins || !out || trials < 1) return fail(PBIT_E_INVALID, "cut/energy: bad argument");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!on_host) {
+        PBIT_CUDA_TRY(launch_cut_energy(*g, spins, trials, out, energy, s));
+        return PBIT_OK;
+    }
+    int64_t* d = nullptr;
+    PBIT_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(int64_t) * (size_t)trials, s));
+    cudaError_t err = launch_cut_energy(*g, spins, trials, d, energy, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(out, d, sizeof(int64_t) * (size_t)trials, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_fail(err, energy ? "energy" : "cut");
+    return PBIT_OK;
+}
+
+pbit_status pbit_cut(pbit_graph g, const int8_t* spins, int32_t trials, int64_t* out, int32_t out_on_host,
+                     void* stream) {
+    return cut_or_energy(g, spins, trials, out, out_on_host, stream, false);
+}
+
+pbit_status pbit_energy(pbit_graph g, const int8_t* spins, int32_t trials, int64_t* out, int32_t out_on_host,
+                        void* stream) {
+    return cut_or_energy(g, spins, trials, out, out_on_host, stream, true);
+}
+
+}  // extern "C"

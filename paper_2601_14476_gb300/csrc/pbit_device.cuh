@@ -1,0 +1,58 @@
+// Device helpers shared by the annealing kernels: the counter-based RNG and
+// the variability p-bit decision (Eqs. 1 and 6 of arXiv 2601.14476).
+#pragma once
+
+#include <cstdint>
+
+namespace pbit {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and key increments
+// 0x9E3779B9 / 0xBB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                        uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// The p-bit input x for an exact integer field D (three placements of the
+// offset; see pbit_offset_mode).  Every operation is an explicitly rounded
+// float32 operation, so the value does not depend on compiler contraction.
+__device__ __forceinline__ float pbit_input(int mode, float I0, float lam, float del, int D) {
+    const float d = (float)D;  // exact: |D| < 2^24
+    if (mode == 1) return __fmul_rn(__fmul_rn(lam, I0), __fadd_rn(d, del));
+    if (mode == 2) return __fmul_rn(lam, __fmaf_rn(I0, d, del));
+    return __fmul_rn(I0, __fmaf_rn(lam, d, del));
+}
+
+// Decision threshold in the 24-bit r-word domain.  With k = word >> 8 and
+// r_k = (2k+1-2^24)/2^24, "tanh(x) - r_k > 0" holds exactly for k < kthr,
+// where kthr = (ceil(t*2^24) + 2^24) / 2 (floor) and t = tanh(x) in float32.
+// Proof: 2k+1-2^24 is an integer, so it is < t*2^24 iff it is < ceil(t*2^24).
+__device__ __forceinline__ uint32_t pbit_kthr(float t) {
+    const int c = (int)ceilf(t * 16777216.0f);  // exact scaling by a power of two
+    return (uint32_t)(c + (1 << 24)) >> 1;
+}
+
+__device__ __forceinline__ uint32_t pbit_kthr_of_x(float x) { return pbit_kthr(tanhf(x)); }
+
+// New state from the r-word, the u-word, the thresholds and the old state.
+__device__ __forceinline__ int pbit_next(uint32_t wr, uint32_t wu, uint32_t kthr, uint32_t thr, int old) {
+    const int cand = ((wr >> 8) < kthr) ? 1 : -1;
+    return ((wu >> 8) < thr) ? cand : old;
+}
+
+}  // namespace pbit

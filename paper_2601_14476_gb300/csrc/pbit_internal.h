@@ -1,0 +1,103 @@
+// Internal declarations shared by the translation units of libpbit.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pbit.h"
+
+namespace pbit {
+
+// Process-wide count of kernels this library has launched (for benchmarks).
+void count_launches(int64_t k);
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const std::string& msg);
+pbit_status fail(pbit_status code, const std::string& msg);
+pbit_status cuda_fail(cudaError_t err, const char* what);
+
+#define PBIT_CUDA_TRY(expr)                                 \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return ::pbit::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ------------------------------------------------------------- the graph ----
+// Device-resident instance: CSR of J = -w (rows sorted by column), biases,
+// and optionally the dense tensor-core operand.
+struct DenseOperand {
+    int32_t n_pad = 0;         // n rounded up to the tile size
+    uint8_t* J_e4m3 = nullptr; // device, tile-ordered e4m3 bytes of J (see pbit_dense.cu)
+    size_t bytes = 0;
+};
+
+struct Graph {
+    int32_t n = 0;
+    int64_t n_edges = 0;
+    int64_t nnz = 0;              // 2 * n_edges
+    int32_t max_degree = 0;
+    bool unit_weights = true;
+    bool has_h = false;
+    int device = 0;
+    double mean_s = 0.0;
+    int64_t total_weight = 0;
+    int32_t max_abs_field = 0;    // max_i |h_i| + sum_j |J_ij|
+    // device arrays
+    int32_t* row_ptr = nullptr;   // [n+1]
+    int32_t* col = nullptr;       // [nnz]
+    int8_t* J = nullptr;          // [nnz]
+    int32_t* h = nullptr;         // [n] or null
+    DenseOperand dense;
+    size_t device_bytes = 0;
+    // host copies used by the schedule and the dense builder
+    std::vector<int32_t> h_row_ptr, h_col;
+    std::vector<int8_t> h_J;
+    std::vector<int32_t> h_h;
+    std::mutex mu;
+};
+
+// Host-side schedule: the float32 I0 table (Methods section).
+pbit_status build_schedule(const Graph& g, double i0_min, double i0_max, int normalize, int steps,
+                           std::vector<float>& out);
+
+// Per-node parameters in the form the kernels read.
+struct NodeParams {
+    const float* lambda = nullptr;   // device [n] or null (1)
+    const float* delta = nullptr;    // device [n] or null (0)
+    const uint32_t* thr = nullptr;   // device [n] update threshold ceil(p*2^24), or null (always)
+};
+
+// Everything one synchronous step needs.
+struct StepArgs {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const int8_t* J;
+    const int32_t* h;
+    NodeParams par;
+    const float* i0_table;
+    int32_t step;
+    const int8_t* in;
+    int8_t* out;
+    int32_t n;
+    int32_t T;
+    uint32_t seed_lo, seed_hi, instance;
+    int32_t offset_mode;
+};
+
+// kernels (pbit_sparse.cu)
+cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* spins,
+                              cudaStream_t s);
+cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
+cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
+                              cudaStream_t s);
+// resident single-CTA anneal: all steps in one launch, spins in shared memory
+bool resident_fits(const Graph& g, int32_t T);
+cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,
+                                   cudaStream_t s);
+
+}  // namespace pbit

@@ -1,0 +1,344 @@
+// Sparse (CSR) kernels: initial state, one synchronous pSA step, the
+// single-CTA resident anneal, exact fields, cut and energy.
+//
+// Spins are trial-major int8 [n][T]: the T trials of node j are contiguous,
+// so the gather of neighbour j for a group of G consecutive trials is one
+// vector load (G = 16: int4, G = 4: 32-bit, G = 1: byte), coalesced across
+// the threads of a warp that share the node.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pbit_device.cuh"
+#include "pbit_internal.h"
+
+namespace pbit {
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int G>
+struct Pack {
+    static constexpr int W = (G + 3) / 4;  // 32-bit words per group
+};
+
+template <int G>
+__device__ __forceinline__ void load_group(const int8_t* p, uint32_t (&w)[Pack<G>::W]) {
+    if constexpr (G == 16) {
+        const int4 v = *reinterpret_cast<const int4*>(p);
+        w[0] = (uint32_t)v.x;
+        w[1] = (uint32_t)v.y;
+        w[2] = (uint32_t)v.z;
+        w[3] = (uint32_t)v.w;
+    } else if constexpr (G == 4) {
+        w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else {
+        w[0] = (uint32_t)(uint8_t)(*p);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void store_group(int8_t* p, const uint32_t (&w)[Pack<G>::W]) {
+    if constexpr (G == 16) {
+        *reinterpret_cast<int4*>(p) = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+    } else if constexpr (G == 4) {
+        *reinterpret_cast<uint32_t*>(p) = w[0];
+    } else {
+        *p = (int8_t)(w[0] & 0xFF);
+    }
+}
+
+__device__ __forceinline__ int sbyte(uint32_t w, int k) { return (int)(int8_t)(uint8_t)(w >> (8 * k)); }
+
+// Exact field of node i for trials t0..t0+G-1 read from `in` (global or shared).
+template <int G>
+__device__ __forceinline__ void gather_field(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                             const int8_t* __restrict__ J, const int8_t* in, int32_t T, int i,
+                                             int t0, int (&acc)[G]) {
+#pragma unroll
+    for (int k = 0; k < G; ++k) acc[k] = 0;
+    const int rb = __ldg(row_ptr + i), re = __ldg(row_ptr + i + 1);
+    for (int e = rb; e < re; ++e) {
+        const int j = __ldg(col + e);
+        const int w = __ldg(J + e);
+        uint32_t v[Pack<G>::W];
+        load_group<G>(in + (size_t)j * T + t0, v);
+#pragma unroll
+        for (int k = 0; k < G; ++k) acc[k] += w * sbyte(v[k >> 2], k & 3);
+    }
+}
+
+// Decisions for one group of G trials of node i at `step` (Eq. 6 p-bit with
+// timing draw), from exact fields acc (without h) and old state words.
+template <int G>
+__device__ __forceinline__ void decide_group(const StepArgs& a, int i, int t0, const int (&acc)[G],
+                                             const uint32_t (&oldw)[Pack<G>::W], uint32_t (&neww)[Pack<G>::W]) {
+    const float I0 = __ldg(a.i0_table + a.step);
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+#pragma unroll
+    for (int k = 0; k < Pack<G>::W; ++k) neww[k] = 0;
+    if constexpr (G == 1) {
+        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
+        const bool odd = t0 & 1;
+        const uint32_t wr = odd ? r.z : r.x, wu = odd ? r.w : r.y;
+        const uint32_t kthr = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[0]));
+        const int s = pbit_next(wr, wu, kthr, thr, sbyte(oldw[0], 0));
+        neww[0] = (uint32_t)(uint8_t)(int8_t)s;
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k += 2) {
+            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo,
+                                   a.seed_hi);
+            const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k]));
+            const uint32_t k1 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k + 1]));
+            const int s0 = pbit_next(r.x, r.y, k0, thr, sbyte(oldw[k >> 2], k & 3));
+            const int s1 = pbit_next(r.z, r.w, k1, thr, sbyte(oldw[k >> 2], (k & 3) + 1));
+            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
+            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ init ----
+__global__ void init_spins_kernel(int32_t n, int32_t T, uint32_t k0, uint32_t k1, uint32_t instance,
+                                  int8_t* __restrict__ spins) {
+    const int64_t total = (int64_t)n * T;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / T), t = (int)(idx - (int64_t)i * T);
+        const uint4 r = philox((uint32_t)i, 0xFFFFFFFFu, (uint32_t)t >> 1, instance, k0, k1);
+        const uint32_t wr = (t & 1) ? r.z : r.x;
+        spins[idx] = ((wr >> 8) < (1u << 23)) ? 1 : -1;  // +1 iff r < 0
+    }
+}
+
+// ------------------------------------------------------------------ step ----
+template <int G>
+__global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
+    const int groups = a.T / G;
+    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    if (tid >= (int64_t)a.n * groups) return;
+    const int i = (int)(tid / groups);
+    const int t0 = (int)(tid - (int64_t)i * groups) * G;
+    int acc[G];
+    gather_field<G>(a.row_ptr, a.col, a.J, a.in, a.T, i, t0, acc);
+    uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
+    load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
+    decide_group<G>(a, i, t0, acc, oldw, neww);
+    store_group<G>(a.out + (size_t)i * a.T + t0, neww);
+}
+
+template <int G>
+cudaError_t launch_step_g(const StepArgs& a, cudaStream_t s) {
+    const int64_t threads = (int64_t)a.n * (a.T / G);
+    const int64_t blocks = (threads + kBlock - 1) / kBlock;
+    sparse_step_kernel<G><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- resident ----
+// One CTA anneals one instance through steps [b, e) with both spin buffers in
+// shared memory; __syncthreads() is the synchronous-update barrier.
+constexpr int kResidentThreads = 512;
+constexpr size_t kResidentSmem = 200 * 1024;
+
+template <int G>
+__global__ void __launch_bounds__(kResidentThreads) resident_kernel(StepArgs a, int32_t step_begin, int32_t step_end) {
+    extern __shared__ __align__(16) int8_t smem[];
+    const int64_t cells = (int64_t)a.n * a.T;
+    int8_t* buf0 = smem;
+    int8_t* buf1 = smem + ((cells + 15) / 16) * 16;
+    for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) buf0[c] = a.in[c];
+    __syncthreads();
+    const int groups = a.T / G;
+    const int64_t items = (int64_t)a.n * groups;
+    int8_t* cur = buf0;
+    int8_t* nxt = buf1;
+    for (int32_t step = step_begin; step < step_end; ++step) {
+        StepArgs sa = a;
+        sa.step = step;
+        for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
+            const int i = (int)(it / groups);
+            const int t0 = (int)(it - (int64_t)i * groups) * G;
+            int acc[G];
+            gather_field<G>(a.row_ptr, a.col, a.J, cur, a.T, i, t0, acc);
+            uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
+            load_group<G>(cur + (size_t)i * a.T + t0, oldw);
+            decide_group<G>(sa, i, t0, acc, oldw, neww);
+            store_group<G>(nxt + (size_t)i * a.T + t0, neww);
+        }
+        __syncthreads();
+        int8_t* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) a.out[c] = cur[c];
+}
+
+template <int G>
+cudaError_t launch_resident_g(const StepArgs& a, int32_t b, int32_t e, cudaStream_t s) {
+    const int64_t cells = (int64_t)a.n * a.T;
+    const size_t smem = 2 * (size_t)(((cells + 15) / 16) * 16);
+    cudaError_t err = cudaFuncSetAttribute(resident_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kResidentSmem);
+    if (err != cudaSuccess) return err;
+    resident_kernel<G><<<1, kResidentThreads, smem, s>>>(a, b, e);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fields ----
+template <int G>
+__global__ void __launch_bounds__(kBlock) fields_kernel(const int32_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const int8_t* __restrict__ J, const int32_t* __restrict__ h,
+                                                        const int8_t* __restrict__ spins, int32_t n, int32_t T,
+                                                        int32_t* __restrict__ out) {
+    const int groups = T / G;
+    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+    if (tid >= (int64_t)n * groups) return;
+    const int i = (int)(tid / groups);
+    const int t0 = (int)(tid - (int64_t)i * groups) * G;
+    int acc[G];
+    gather_field<G>(row_ptr, col, J, spins, T, i, t0, acc);
+    const int hi = h ? h[i] : 0;
+#pragma unroll
+    for (int k = 0; k < G; ++k) out[(size_t)i * T + t0 + k] = hi + acc[k];
+}
+
+// ------------------------------------------------------------ cut/energy ----
+// Block = 8 warps over a slab of 32*G trials (lane l owns trials l*G..l*G+G-1
+// of the slab) and a range of rows.  Per trial it accumulates
+//   cut:    sum over directed CSR entries of J_ij (s_i s_j - 1)   (= 4 * cut)
+//   energy: -2 h_i s_i - sum over directed entries J_ij s_i s_j   (= 2 * H)
+// reduces across the warps in shared memory and adds one int64 per trial.
+constexpr int kRowsPerBlock = 128;
+
+template <int G>
+__global__ void __launch_bounds__(kBlock) cut_energy_kernel(const int32_t* __restrict__ row_ptr,
+                                                            const int32_t* __restrict__ col,
+                                                            const int8_t* __restrict__ J,
+                                                            const int32_t* __restrict__ h,
+                                                            const int8_t* __restrict__ spins, int32_t n, int32_t T,
+                                                            bool energy, unsigned long long* __restrict__ out) {
+    __shared__ long long red[kBlock / 32][32 * G];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t0 = blockIdx.y * 32 * G + lane * G;
+    const bool active = t0 < T;
+    long long acc[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) acc[k] = 0;
+    const int r0 = blockIdx.x * kRowsPerBlock;
+    const int r1 = min(n, r0 + kRowsPerBlock);
+    if (active) {
+        for (int i = r0 + warp; i < r1; i += kBlock / 32) {
+            uint32_t own[Pack<G>::W];
+            load_group<G>(spins + (size_t)i * T + t0, own);
+            int part[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) part[k] = 0;
+            const int rb = row_ptr[i], re = row_ptr[i + 1];
+            for (int e = rb; e < re; ++e) {
+                const int j = col[e];
+                const int w = J[e];
+                uint32_t v[Pack<G>::W];
+                load_group<G>(spins + (size_t)j * T + t0, v);
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const int ss = sbyte(own[k >> 2], k & 3) * sbyte(v[k >> 2], k & 3);
+                    part[k] += energy ? -w * ss : w * (ss - 1);
+                }
+            }
+            const int hi = (energy && h) ? h[i] : 0;
+#pragma unroll
+            for (int k = 0; k < G; ++k) acc[k] += (long long)part[k] - 2LL * hi * sbyte(own[k >> 2], k & 3);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k) red[warp][lane * G + k] = acc[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < 32 * G; c += kBlock) {
+        long long s = 0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += red[w][c];
+        const int t = blockIdx.y * 32 * G + c;
+        if (t < T) atomicAdd(out + t, (unsigned long long)s);
+    }
+}
+
+__global__ void finish_cut_energy(long long* v, int32_t T, bool energy) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) v[t] = energy ? v[t] / 2 : v[t] / 4;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers ----
+cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* spins,
+                              cudaStream_t s) {
+    const int64_t total = (int64_t)n * T;
+    int64_t blocks = (total + kBlock - 1) / kBlock;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    init_spins_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(n, T, (uint32_t)(seed & 0xFFFFFFFFu),
+                                                           (uint32_t)(seed >> 32), instance, spins);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s) {
+    if (a.T % 16 == 0 && aligned16(a.in) && aligned16(a.out)) return launch_step_g<16>(a, s);
+    if (a.T % 4 == 0 && aligned4(a.in) && aligned4(a.out)) return launch_step_g<4>(a, s);
+    return launch_step_g<1>(a, s);
+}
+
+bool resident_fits(const Graph& g, int32_t T) {
+    const int64_t cells = (int64_t)g.n * T;
+    return 2 * (((cells + 15) / 16) * 16) <= (int64_t)kResidentSmem;
+}
+
+cudaError_t launch_resident_anneal(const StepArgs& a, int32_t b, int32_t e, cudaStream_t s) {
+    if (a.T % 4 == 0) return launch_resident_g<4>(a, b, e, s);
+    return launch_resident_g<1>(a, b, e, s);
+}
+
+cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s) {
+    const bool g4 = T % 4 == 0 && aligned4(spins);
+    const int G = g4 ? 4 : 1;
+    const int64_t threads = (int64_t)g.n * (T / G);
+    const int64_t blocks = (threads + kBlock - 1) / kBlock;
+    if (g4)
+        fields_kernel<4><<<(unsigned)blocks, kBlock, 0, s>>>(g.row_ptr, g.col, g.J, g.h, spins, g.n, T, fields);
+    else
+        fields_kernel<1><<<(unsigned)blocks, kBlock, 0, s>>>(g.row_ptr, g.col, g.J, g.h, spins, g.n, T, fields);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
+                              cudaStream_t s) {
+    cudaError_t err = cudaMemsetAsync(out, 0, sizeof(int64_t) * (size_t)T, s);
+    if (err != cudaSuccess) return err;
+    const bool g4 = T % 4 == 0 && aligned4(spins);
+    const int G = g4 ? 4 : 1;
+    dim3 grid((unsigned)((g.n + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)((T + 32 * G - 1) / (32 * G)));
+    auto* o = reinterpret_cast<unsigned long long*>(out);
+    if (g4)
+        cut_energy_kernel<4><<<grid, kBlock, 0, s>>>(g.row_ptr, g.col, g.J, g.h, spins, g.n, T, energy, o);
+    else
+        cut_energy_kernel<1><<<grid, kBlock, 0, s>>>(g.row_ptr, g.col, g.J, g.h, spins, g.n, T, energy, o);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    finish_cut_energy<<<(T + 255) / 256, 256, 0, s>>>(reinterpret_cast<long long*>(out), T, energy);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace pbit

@@ -1,0 +1,214 @@
+"""GPU parity of the sparse / resident CUDA path against the CPU oracle.
+
+Bit-exact: initial state, fields, cuts, energies, schedule.  Decisions: the
+kernel takes the p-bit decision in float32 (tanhf), the oracle in FP64; a
+decision may differ only where |tanh(x) - r| < 1e-6, and such mismatches must
+be rarer than 1e-6 of all decisions.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_14476_gb300 import inputs, pbit
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-6
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+GRAPHS = {
+    "gnm800": lambda: inputs.erdos_renyi_gnm(800, 19176, 1, "+1"),
+    "torus": lambda: inputs.torus_2d(12, 20, 2, "pm1"),
+    "complete": lambda: inputs.complete_pm1(300, 3),
+    "rgg": lambda: inputs.rgg_knn(700, 4, 3, "pm1"),
+}
+
+
+def _int8_weights(g, seed):
+    g.w = np.random.default_rng(seed).integers(-127, 128, g.m).astype(np.int8)
+    return g
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("T", [16, 12, 7, 1])
+def test_fields_cut_energy_bit_exact(name, T):
+    g = GRAPHS[name]()
+    if name == "rgg":
+        g = _int8_weights(g, 5)
+    h = np.random.default_rng(9).integers(-30, 31, g.n).astype(np.int32)
+    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, T, 4)
+    d = _dev(s)
+    assert np.array_equal(_host(G.fields(d)).astype(np.int64), oracle.fields(csr, s, h))
+    assert np.array_equal(G.energy(d), oracle.energy(csr, s, h))
+    G0 = pbit.Graph(g.n, g.src, g.dst, g.w)
+    assert np.array_equal(G0.cut(d), oracle.cut(g.src, g.dst, g.w, s))
+
+
+@pytest.mark.parametrize("T", [16, 5, 64])
+def test_init_spins_bit_exact(T):
+    g = inputs.torus_2d(10, 30, 1)
+    G = pbit.Graph.from_inputs(g)
+    out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+    pbit.pbit_init_spins(G.handle, T, 0x1234_5678_9ABC, 7, out)
+    assert np.array_equal(_host(out), oracle.init_spins(g.n, T, 0x1234_5678_9ABC, 7))
+
+
+def test_schedule_bit_exact():
+    g = inputs.erdos_renyi_gnm(800, 19176, 1, "+1")
+    G = pbit.Graph.from_inputs(g)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    assert np.array_equal(G.schedule(0.1, 10.0, 1000), oracle.schedule(csr, 0.1, 10.0, 1000))
+    assert G.info()["mean_s"] == oracle.mean_s(csr)
+
+
+def _lockstep(g, T, steps, var, kernel, seed=11, instance=3, mode=pbit.OFFSET_NORTHSTAR, c=(0.1, 10.0), S=None):
+    """Advance one step at a time on the GPU; check each step against the oracle from the GPU's state."""
+    G = pbit.Graph.from_inputs(g)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    S = S or steps
+    tab = oracle.schedule(csr, c[0], c[1], S)
+    state = oracle.init_spins(g.n, T, seed, instance)
+    decisions = mismatches = 0
+    worst = 0.0
+    for t in range(steps):
+        d_in = _dev(state)
+        d_out = torch.empty_like(d_in)
+        p, keep = pbit.make_params(T, S, step_begin=t, step_end=t + 1, i0_min=c[0], i0_max=c[1], seed=seed,
+                                   instance=instance, kernel=kernel, variability=var, offset_mode=mode)
+        pbit.pbit_anneal(G.handle, p, d_in, d_out)
+        gpu = _host(d_out)
+        want, gap = oracle.step(csr, state, t, tab[t], seed, instance, variability=var, offset_mode=mode,
+                                want_gap=True)
+        bad = gpu != want
+        decisions += state.size
+        mismatches += int(bad.sum())
+        if bad.any():
+            worst = max(worst, float(np.abs(gap[bad]).max()))
+        state = gpu
+    return decisions, mismatches, worst
+
+
+@pytest.mark.parametrize("kernel", [pbit.KERNEL_SPARSE, pbit.KERNEL_RESIDENT])
+@pytest.mark.parametrize("mode", [pbit.OFFSET_NORTHSTAR, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+def test_lockstep_decisions(kernel, mode):
+    g = inputs.erdos_renyi_gnm(400, 3000, 2, "pm1")
+    var = inputs.variability(g.n, 2, s_intensity=0.3, s_offset=0.3)
+    dec, mis, worst = _lockstep(g, 32, 30, var, kernel, mode=mode)
+    assert mis == 0 or worst < BAND, (mis, worst)
+    assert mis <= max(1, dec * 1e-6) * 3
+
+
+@pytest.mark.parametrize("T", [1, 3, 16, 20])
+def test_lockstep_ragged_trials(T):
+    g = inputs.rgg_knn(333, 7, 3, "pm1")
+    var = inputs.variability(g.n, 7)
+    dec, mis, worst = _lockstep(g, T, 12, var, pbit.KERNEL_SPARSE)
+    assert mis == 0 or worst < BAND
+
+
+def test_resident_equals_sparse_full_run():
+    g = inputs.erdos_renyi_gnm(800, 19176, 1, "+1")
+    G = pbit.Graph.from_inputs(g)
+    outs = []
+    for kernel in (pbit.KERNEL_SPARSE, pbit.KERNEL_RESIDENT):
+        outs.append(_host(G.anneal(16, 300, seed=5, kernel=kernel)))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_resume_identity_and_in_place():
+    g = inputs.torus_2d(10, 16, 3)
+    var = inputs.variability(g.n, 3)
+    G = pbit.Graph.from_inputs(g)
+    T, S = 32, 41
+    full = _host(G.anneal(T, S, seed=2, variability=var, kernel=pbit.KERNEL_SPARSE))
+    a = G.anneal(T, S, step_end=17, seed=2, variability=var, kernel=pbit.KERNEL_SPARSE)
+    # resume in place (odd and even remaining counts)
+    p, keep = pbit.make_params(T, S, step_begin=17, step_end=30, seed=2, variability=var, kernel=pbit.KERNEL_SPARSE)
+    pbit.pbit_anneal(G.handle, p, a, a)
+    p, keep = pbit.make_params(T, S, step_begin=30, step_end=S, seed=2, variability=var, kernel=pbit.KERNEL_SPARSE)
+    pbit.pbit_anneal(G.handle, p, a, a)
+    assert np.array_equal(_host(a), full)
+    # an empty range copies the input
+    b = torch.empty_like(a)
+    p, keep = pbit.make_params(T, S, step_begin=5, step_end=5, seed=2)
+    pbit.pbit_anneal(G.handle, p, a, b)
+    assert np.array_equal(_host(b), full)
+
+
+def test_hold_and_zero_edge_graph():
+    g = inputs.torus_2d(5, 7, 1)
+    G = pbit.Graph.from_inputs(g)
+    s = inputs.random_spins(g.n, 8, 1)
+    var = {"p_update": np.zeros(g.n, np.float32)}
+    out = G.anneal(8, 20, spins_in=_dev(s), seed=1, variability=var, kernel=pbit.KERNEL_SPARSE)
+    assert np.array_equal(_host(out), s)
+    # a graph with no edges: cut 0, decisions are fair coins, normalisation is rejected
+    E = pbit.Graph(9, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8))
+    out = E.anneal(64, 5, seed=1, i0_normalize=0, kernel=pbit.KERNEL_SPARSE)
+    assert np.all(E.cut(out) == 0)
+    with pytest.raises(pbit.PbitError):
+        E.anneal(64, 5, seed=1)
+
+
+def test_full_run_matches_oracle_mean_cut():
+    """Plain G(800,19176) workload: per-trial cuts equal the oracle's except trials a near-tie diverged."""
+    w = inputs.plain_er800()
+    g = w.graph
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
+    G = pbit.Graph.from_inputs(g)
+    out = G.anneal(w.trials, w.steps, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed)
+    gpu_cut = G.cut(out)
+    ref = oracle.anneal(csr, oracle.init_spins(g.n, w.trials, w.seed), tab, w.seed)
+    ref_cut = oracle.cut(g.src, g.dst, g.w, ref)
+    same = (gpu_cut == ref_cut).mean()
+    assert same >= 0.75, (gpu_cut, ref_cut)
+    assert abs(gpu_cut.mean() - ref_cut.mean()) <= 0.005 * max(1.0, abs(ref_cut.mean())) or same == 1.0
+
+
+def test_full_size_torus_sampled():
+    """100x200 torus, 1024 trials, in the bench launch configuration: sampled decisions vs oracle."""
+    w = inputs.sparse_torus20000()
+    g = w.graph
+    G = pbit.Graph.from_inputs(g)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
+    k = 3000  # a mid-schedule step
+    state = G.anneal(w.trials, w.steps, step_end=k, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed,
+                     variability=w.var)
+    nxt = torch.empty_like(state)
+    p, keep = pbit.make_params(w.trials, w.steps, step_begin=k, step_end=k + 1, i0_min=w.c_min, i0_max=w.c_max,
+                               seed=w.seed, variability=w.var)
+    pbit.pbit_anneal(G.handle, p, state, nxt)
+    s_host, n_host = _host(state), _host(nxt)
+    rng = np.random.default_rng(0)
+    nodes = rng.integers(0, g.n, 20000).astype(np.int32)
+    trials = rng.integers(0, w.trials, 20000).astype(np.int32)
+    want, gap = oracle.step_sampled(csr, s_host, nodes, trials, k, tab[k], w.seed, variability=w.var)
+    bad = n_host[nodes, trials] != want
+    assert not bad.any() or np.abs(gap[bad]).max() < BAND
+    # the exact observables at full size
+    cuts = G.cut(nxt)
+    assert np.array_equal(cuts, oracle.cut(g.src, g.dst, g.w, n_host))
+
+
+def test_mismatch_rate_below_bound():
+    """Lockstep over > 1e7 decisions: mismatches only in the band, and fewer than 1e-6 of decisions."""
+    g = inputs.torus_2d(50, 100, 9, "pm1")
+    var = inputs.variability(g.n, 9)
+    dec, mis, worst = _lockstep(g, 256, 12, var, pbit.KERNEL_SPARSE, S=100)
+    assert dec >= 1.5e7
+    assert mis == 0 or worst < BAND
+    assert mis < 1e-6 * dec
