@@ -166,10 +166,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "sparse", "dense", "resident"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--anneal-steps", type=int, default=0,
+                    help="shorten the schedule (profiling captures only; such a line is not a bench value)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     w = workload(args.config)
+    if args.anneal_steps > 0:
+        w.steps = args.anneal_steps
+        w.name += f"_first{args.anneal_steps}steps"
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -252,7 +258,7 @@ def main():
     e2e_ms = []
     h2d = g.m * (4 + 4 + 1) + (3 * g.n * 4 if w.var else 0) + S * 4
     d2h = T * 8
-    for it in range(2 + args.steps):
+    for it in range(0 if args.no_e2e else 2 + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         G2 = pbit.Graph.from_inputs(g, dense=(args.config == "dense"))
@@ -266,7 +272,9 @@ def main():
         G2.close()
         if it >= 2:
             e2e_ms.append(dt * 1e3)
-    e2e_val = world * upd_run / (np.mean(e2e_ms) * 1e-3)
+    e2e_val = world * upd_run / (np.mean(e2e_ms) * 1e-3) if e2e_ms else None
+    if not e2e_ms:
+        host_cuts = cuts.cpu().numpy()
 
     if rank != 0:
         if dist:
