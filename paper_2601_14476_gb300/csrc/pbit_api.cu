@@ -207,8 +207,6 @@ static pbit_status build_host(Graph& g, int32_t n, int64_t n_edges, const int32_
 
 using namespace pbit;
 
-struct pbit_graph_s : public Graph {};
-
 extern "C" {
 
 const char* pbit_last_error(void) { return g_last_error.c_str(); }

@@ -101,3 +101,6 @@ cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int
                                    cudaStream_t s);
 
 }  // namespace pbit
+
+// The opaque C handle is the internal Graph.
+struct pbit_graph_s : public pbit::Graph {};

@@ -75,6 +75,7 @@ def _declare(lib):
         "pbit_mean_s": ([i32, i64, _P, _P, _P, _P], C.c_int),
         "pbit_anneal_params_default": ([_P], None),
         "pbit_anneal": ([_P, _P, _P, _P], C.c_int),
+        "pbit_anneal_noalloc": ([_P, _P, _P, _P], C.c_int),
         "pbit_init_spins": ([_P, i32, u64, u32, _P, _P], C.c_int),
         "pbit_fields": ([_P, _P, i32, _P, _P], C.c_int),
         "pbit_cut": ([_P, _P, i32, _P, i32, _P], C.c_int),
@@ -214,6 +215,11 @@ def make_params(trials, steps, step_begin=0, step_end=0, i0_min=0.1, i0_max=10.0
 
 def pbit_anneal(g, params, spins_in, spins_out):
     _check(lib().pbit_anneal(g, C.byref(params), _dev(spins_in), _dev(spins_out)))
+
+
+def pbit_anneal_noalloc(g, params, spins_in, spins_out):
+    """pbit_anneal with its scratch in the library's fixed device array (no allocation)."""
+    _check(lib().pbit_anneal_noalloc(g, C.byref(params), _dev(spins_in), _dev(spins_out)))
 
 
 def pbit_init_spins(g, trials, seed, instance, spins, stream=None):
