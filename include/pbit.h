@@ -215,6 +215,21 @@ pbit_status pbit_init_spins(pbit_graph g, int32_t trials, uint64_t seed, uint32_
 pbit_status pbit_fields(pbit_graph g, const int8_t* spins, int32_t trials, int32_t* fields, void* stream);
 
 /*
+ * The same fields computed by the tensor-core kernel (needs a graph created
+ * with PBIT_GRAPH_DENSE and trials % 32 == 0, trials <= 256 or % 256 == 0):
+ * J as e4m3 tiles times the spins as e4m3, FP32 accumulation, exact because
+ * |J| <= 16 and every partial sum is an integer below 2^24.  DEVICE int32[n*T].
+ */
+pbit_status pbit_fields_dense(pbit_graph g, const int8_t* spins, int32_t trials, int32_t* fields, void* stream);
+
+/*
+ * Synchronise `stream` and report whether any kernel of this graph gave up a
+ * bounded device-side wait since the last call (PBIT_E_TIMEOUT; the results
+ * of that work are undefined).  Clears the flag.
+ */
+pbit_status pbit_graph_status(pbit_graph g, void* stream);
+
+/*
  * Per-trial cut = sum over edges of w * [sigma_src != sigma_dst], and energy
  * H = -sum_i h_i sigma_i - sum_{i<j} J_ij sigma_i sigma_j, exact int64.
  * `out` is HOST int64[T] (the call synchronises `stream`) when out_on_host

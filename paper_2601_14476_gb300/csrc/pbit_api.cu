@@ -95,6 +95,7 @@ static void release(Graph* g) {
     cudaFree(g->J);
     cudaFree(g->h);
     cudaFree(g->dense.J_e4m3);
+    cudaFree(g->err);
     cudaSetDevice(cur);
 }
 
@@ -228,7 +229,15 @@ pbit_status pbit_graph_create(int32_t n, int64_t n_edges, const int32_t* src, co
     if ((st = upload(&g->col, g->h_col.data(), (size_t)g->nnz, g->device_bytes)) != PBIT_OK) goto err;
     if ((st = upload(&g->J, g->h_J.data(), (size_t)g->nnz, g->device_bytes)) != PBIT_OK) goto err;
     if (h && (st = upload(&g->h, h, (size_t)n, g->device_bytes)) != PBIT_OK) goto err;
-    (void)flags;
+    if ((st = upload(&g->err, (const int*)nullptr, 1, g->device_bytes)) != PBIT_OK) goto err;
+    {
+        cudaError_t ce = cudaMemset(g->err, 0, sizeof(int));
+        if (ce != cudaSuccess) {
+            st = cuda_fail(ce, "cudaMemset(err)");
+            goto err;
+        }
+    }
+    if ((flags & PBIT_GRAPH_DENSE) && (st = build_dense_operand(*g)) != PBIT_OK) goto err;
     *out = g.release();
     return PBIT_OK;
 err:
@@ -323,10 +332,16 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     const int64_t cells = (int64_t)g->n * T;
 
     int kernel = p->kernel;
-    if (kernel == PBIT_KERNEL_DENSE) return fail(PBIT_E_UNSUPPORTED, "anneal: dense kernel not available");
+    std::string why;
+    if (kernel == PBIT_KERNEL_DENSE && !dense_shape_ok(*g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
     if (kernel == PBIT_KERNEL_RESIDENT && !resident_fits(*g, T))
         return fail(PBIT_E_UNSUPPORTED, "anneal: n*T too large for the shared-memory resident kernel");
-    if (kernel == PBIT_KERNEL_AUTO) kernel = resident_fits(*g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
+    if (kernel == PBIT_KERNEL_AUTO) {
+        if (dense_shape_ok(*g, T, nullptr))
+            kernel = PBIT_KERNEL_DENSE;
+        else
+            kernel = resident_fits(*g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
+    }
 
     // host-side tables
     std::vector<float> tab;
@@ -401,6 +416,22 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         PBIT_CUDA_TRY(launch_resident_anneal(a, b, e, s));
         return PBIT_OK;
     }
+    if (kernel == PBIT_KERNEL_DENSE) {
+        // tiled e4m3 spin buffers; convert in, step, convert out
+        uint8_t* t0 = nullptr;
+        uint8_t* t1 = nullptr;
+        const size_t tb = dense_spin_bytes(*g, T);
+        if ((st = cb.alloc(&t0, tb)) != PBIT_OK) return st;
+        if ((st = cb.alloc(&t1, tb)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(launch_to_tiled(*g, cur, T, t0, s));
+        for (int32_t j = b; j < e; ++j) {
+            a.step = j;
+            PBIT_CUDA_TRY(launch_dense_step(*g, a, t0, t1, nullptr, g->err, s));
+            std::swap(t0, t1);
+        }
+        PBIT_CUDA_TRY(launch_from_tiled(*g, t0, T, spins_out, s));
+        return PBIT_OK;
+    }
     // Jacobi rotation: step j writes spins_out when (k-1-j) is even, else scratch
     int8_t* scratch = nullptr;
     const int32_t k = e - b;
@@ -428,6 +459,40 @@ pbit_status pbit_fields(pbit_graph g, const int8_t* spins, int32_t trials, int32
     pbit_status st = check_device(g);
     if (st != PBIT_OK) return st;
     PBIT_CUDA_TRY(launch_fields(*g, spins, trials, fields, (cudaStream_t)stream));
+    return PBIT_OK;
+}
+
+pbit_status pbit_fields_dense(pbit_graph g, const int8_t* spins, int32_t trials, int32_t* fields, void* stream) {
+    if (!g || !spins || !fields || trials < 1) return fail(PBIT_E_INVALID, "fields_dense: bad argument");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    std::string why;
+    if (!dense_shape_ok(*g, trials, &why)) return fail(PBIT_E_UNSUPPORTED, "fields_dense: " + why);
+    cudaStream_t s = (cudaStream_t)stream;
+    CallBuffers cb;
+    cb.s = s;
+    uint8_t* t0 = nullptr;
+    if ((st = cb.alloc(&t0, dense_spin_bytes(*g, trials))) != PBIT_OK) return st;
+    PBIT_CUDA_TRY(launch_to_tiled(*g, spins, trials, t0, s));
+    StepArgs a{};
+    a.T = trials;
+    PBIT_CUDA_TRY(launch_dense_step(*g, a, t0, nullptr, fields, g->err, s));
+    return PBIT_OK;
+}
+
+pbit_status pbit_graph_status(pbit_graph g, void* stream) {
+    if (!g) return fail(PBIT_E_INVALID, "graph_status: NULL graph");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int host = 0;
+    PBIT_CUDA_TRY(cudaMemcpyAsync(&host, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PBIT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (host != 0) {
+        PBIT_CUDA_TRY(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+        PBIT_CUDA_TRY(cudaStreamSynchronize(s));
+        return fail(PBIT_E_TIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(host) + ")");
+    }
     return PBIT_OK;
 }
 

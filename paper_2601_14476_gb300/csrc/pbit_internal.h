@@ -52,6 +52,7 @@ struct Graph {
     int8_t* J = nullptr;          // [nnz]
     int32_t* h = nullptr;         // [n] or null
     DenseOperand dense;
+    int* err = nullptr;           // device word: nonzero after a bounded wait gave up
     size_t device_bytes = 0;
     // host copies used by the schedule and the dense builder
     std::vector<int32_t> h_row_ptr, h_col;
@@ -95,6 +96,14 @@ cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
 cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
                               cudaStream_t s);
+// dense tensor-core path (pbit_dense.cu)
+bool dense_shape_ok(const Graph& g, int32_t T, std::string* why);
+pbit_status build_dense_operand(Graph& g);
+size_t dense_spin_bytes(const Graph& g, int32_t T);
+cudaError_t launch_to_tiled(const Graph& g, const int8_t* s, int32_t T, uint8_t* out, cudaStream_t st);
+cudaError_t launch_from_tiled(const Graph& g, const uint8_t* in, int32_t T, int8_t* s, cudaStream_t st);
+cudaError_t launch_dense_step(const Graph& g, const StepArgs& sa, const uint8_t* tin, uint8_t* tout,
+                              int32_t* fields_out, int* err, cudaStream_t st);
 // resident single-CTA anneal: all steps in one launch, spins in shared memory
 bool resident_fits(const Graph& g, int32_t T);
 cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,

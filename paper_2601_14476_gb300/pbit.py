@@ -78,6 +78,8 @@ def _declare(lib):
         "pbit_anneal_noalloc": ([_P, _P, _P, _P], C.c_int),
         "pbit_init_spins": ([_P, i32, u64, u32, _P, _P], C.c_int),
         "pbit_fields": ([_P, _P, i32, _P, _P], C.c_int),
+        "pbit_fields_dense": ([_P, _P, i32, _P, _P], C.c_int),
+        "pbit_graph_status": ([_P, _P], C.c_int),
         "pbit_cut": ([_P, _P, i32, _P, i32, _P], C.c_int),
         "pbit_energy": ([_P, _P, i32, _P, i32, _P], C.c_int),
     }
@@ -231,6 +233,14 @@ def pbit_fields(g, spins, trials, fields, stream=None):
     _check(lib().pbit_fields(g, _dev(spins), int(trials), _dev(fields), _stream(stream)))
 
 
+def pbit_fields_dense(g, spins, trials, fields, stream=None):
+    _check(lib().pbit_fields_dense(g, _dev(spins), int(trials), _dev(fields), _stream(stream)))
+
+
+def pbit_graph_status(g, stream=None):
+    _check(lib().pbit_graph_status(g, _stream(stream)))
+
+
 def pbit_cut(g, spins, trials, stream=None) -> np.ndarray:
     out = np.zeros(int(trials), np.int64)
     _check(lib().pbit_cut(g, _dev(spins), int(trials), out.ctypes.data_as(_P), 1, _stream(stream)))
@@ -294,6 +304,15 @@ class Graph:
         out = torch.empty(spins.shape, dtype=torch.int32, device=spins.device)
         pbit_fields(self.handle, spins, spins.shape[1], out, stream)
         return out
+
+    def fields_dense(self, spins, stream=None):
+        import torch
+        out = torch.empty(spins.shape, dtype=torch.int32, device=spins.device)
+        pbit_fields_dense(self.handle, spins, spins.shape[1], out, stream)
+        return out
+
+    def status(self, stream=None):
+        pbit_graph_status(self.handle, stream)
 
     def schedule(self, i0_min, i0_max, steps, normalize=True):
         return pbit_schedule(self.handle, i0_min, i0_max, 1 if normalize else 0, steps)

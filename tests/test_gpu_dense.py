@@ -1,0 +1,146 @@
+"""GPU parity of the tensor-core (tcgen05, e4m3 x e4m3 -> f32) dense path.
+
+Fields are exact integers and must equal the oracle bit for bit, including
+the extreme sums (|J| = 16 everywhere, all spins aligned).  The fused update
+uses the same float32 decision as the sparse kernel, so whole anneals agree
+with the sparse path exactly, and with the oracle up to the 1e-6 tie band.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_14476_gb300 import inputs, pbit
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-6
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _complete(n, seed, lo=-1, hi=1, zero_ok=False):
+    g = inputs.complete_pm1(n, seed)
+    if (lo, hi) != (-1, 1):
+        rng = np.random.default_rng(seed)
+        w = rng.integers(lo, hi + 1, g.m).astype(np.int8)
+        if not zero_ok:
+            w[w == 0] = 1
+        g.w = w
+    return g
+
+
+@pytest.mark.parametrize("n,T", [(200, 32), (256, 64), (300, 256), (513, 96), (1000, 512), (2000, 256)])
+def test_dense_fields_bit_exact(n, T):
+    g = _complete(n, n)
+    G = pbit.Graph.from_inputs(g, dense=True)
+    assert G.info()["has_dense"] == 1
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(g.n, T, 3)
+    got = _host(G.fields_dense(_dev(s))).astype(np.int64)
+    assert np.array_equal(got, oracle.fields(csr, s))
+    G.status()
+
+
+def test_dense_fields_extreme_and_int_weights():
+    # |J| = 16 everywhere with aligned spins: |D| = 16 (n - 1), the largest sums
+    n, T = 777, 32
+    g = _complete(n, 1)
+    g.w = np.full(g.m, -16, np.int8)
+    h = np.arange(n, dtype=np.int32) - 300
+    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h, dense=True)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = np.ones((n, T), np.int8)
+    s[:, 1::2] = -1
+    assert np.array_equal(_host(G.fields_dense(_dev(s))).astype(np.int64), oracle.fields(csr, s, h))
+    # random weights in [-16, 16] (zeros included) on a sparse graph held densely
+    e = inputs.erdos_renyi_gnm(900, 20000, 4, "+1")
+    e.w = np.random.default_rng(4).integers(-16, 17, e.m).astype(np.int8)
+    G = pbit.Graph.from_inputs(e, dense=True)
+    csr = oracle.Csr(e.n, e.src, e.dst, e.w)
+    s = inputs.random_spins(e.n, 64, 5)
+    assert np.array_equal(_host(G.fields_dense(_dev(s))).astype(np.int64), oracle.fields(csr, s))
+
+
+def test_dense_operand_rejections():
+    g = _complete(100, 2)
+    g.w[0] = 17
+    with pytest.raises(pbit.PbitError):
+        pbit.Graph.from_inputs(g, dense=True)
+    G = pbit.Graph.from_inputs(_complete(100, 2), dense=True)
+    with pytest.raises(pbit.PbitError) as ei:
+        G.anneal(48, 10, kernel=pbit.KERNEL_DENSE)
+    assert ei.value.code == pbit.PBIT_E_UNSUPPORTED
+    S = pbit.Graph.from_inputs(_complete(100, 2))
+    with pytest.raises(pbit.PbitError) as ei:
+        S.anneal(64, 10, kernel=pbit.KERNEL_DENSE)
+    assert ei.value.code == pbit.PBIT_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n,T", [(300, 64), (2000, 256)])
+def test_dense_anneal_equals_sparse_anneal(n, T):
+    g = _complete(n, 7)
+    var = inputs.variability(n, 7, s_intensity=0.3, s_offset=0.3)
+    G = pbit.Graph.from_inputs(g, dense=True)
+    kw = dict(seed=3, variability=var, i0_min=0.05, i0_max=5.0)
+    d = _host(G.anneal(T, 60, kernel=pbit.KERNEL_DENSE, **kw))
+    s = _host(G.anneal(T, 60, kernel=pbit.KERNEL_SPARSE, **kw))
+    assert np.array_equal(d, s)
+    G.status()
+
+
+@pytest.mark.parametrize("mode", [pbit.OFFSET_NORTHSTAR, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+def test_dense_lockstep_vs_oracle(mode):
+    n, T, S = 400, 64, 40
+    g = _complete(n, 11)
+    var = inputs.variability(n, 11, s_intensity=0.3, s_offset=0.3)
+    G = pbit.Graph.from_inputs(g, dense=True)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, 0.05, 5.0, S)
+    state = oracle.init_spins(n, T, 5, 2)
+    mis = 0
+    for t in range(0, S, 3):
+        d_in = _dev(state)
+        d_out = torch.empty_like(d_in)
+        p, keep = pbit.make_params(T, S, step_begin=t, step_end=t + 1, i0_min=0.05, i0_max=5.0, seed=5,
+                                   instance=2, kernel=pbit.KERNEL_DENSE, variability=var, offset_mode=mode)
+        pbit.pbit_anneal(G.handle, p, d_in, d_out)
+        gpu = _host(d_out)
+        want, gap = oracle.step(csr, state, t, tab[t], 5, 2, variability=var, offset_mode=mode, want_gap=True)
+        bad = gpu != want
+        assert not bad.any() or np.abs(gap[bad]).max() < BAND
+        mis += int(bad.sum())
+        state = gpu
+    assert mis <= 2
+
+
+def test_dense_full_size_sampled():
+    """K_2000, 256 trials, the bench configuration: sampled decisions at a mid-schedule step."""
+    w = inputs.dense_k2000()
+    g = w.graph
+    G = pbit.Graph.from_inputs(g, dense=True)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
+    k = 1200
+    state = G.anneal(w.trials, w.steps, step_end=k, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed,
+                     variability=w.var)
+    nxt = torch.empty_like(state)
+    p, keep = pbit.make_params(w.trials, w.steps, step_begin=k, step_end=k + 1, i0_min=w.c_min, i0_max=w.c_max,
+                               seed=w.seed, variability=w.var)
+    pbit.pbit_anneal(G.handle, p, state, nxt)
+    s_host, n_host = _host(state), _host(nxt)
+    rng = np.random.default_rng(1)
+    nodes = rng.integers(0, g.n, 3000).astype(np.int32)
+    trials = rng.integers(0, w.trials, 3000).astype(np.int32)
+    want, gap = oracle.step_sampled(csr, s_host, nodes, trials, k, tab[k], w.seed, variability=w.var)
+    bad = n_host[nodes, trials] != want
+    assert not bad.any() or np.abs(gap[bad]).max() < BAND
+    assert np.array_equal(G.cut(nxt), oracle.cut(g.src, g.dst, g.w, n_host))
+    G.status()
