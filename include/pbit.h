@@ -67,7 +67,7 @@ int64_t pbit_launch_count(void);
 
 typedef struct pbit_graph_s* pbit_graph;
 
-#define PBIT_GRAPH_DENSE 1u     /* also build the dense tensor-core operand of J */
+#define PBIT_GRAPH_DENSE 1u     /* also build the dense tensor-core operand of J (|w| <= 16, n <= 8192) */
 
 /*
  * Create a MAX-CUT instance on the current CUDA device.
@@ -203,6 +203,15 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
 pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in,
                                 int8_t* spins_out);
 
+/*
+ * The kernel pbit_anneal runs for `requested` (a pbit_kernel) and `trials`
+ * on this graph: AUTO resolves to DENSE when the graph holds the dense
+ * operand and the trial count suits it, else RESIDENT when both spin buffers
+ * fit one CTA's shared memory, else SPARSE.  PBIT_E_UNSUPPORTED if a forced
+ * kernel cannot run the shape.
+ */
+pbit_status pbit_select_kernel(pbit_graph g, int32_t requested, int32_t trials, int32_t* kernel);
+
 /* Write the Philox initial state of (seed, instance) to DEVICE int8[n*T]. */
 pbit_status pbit_init_spins(pbit_graph g, int32_t trials, uint64_t seed, uint32_t instance, int8_t* spins,
                             void* stream);
@@ -216,7 +225,7 @@ pbit_status pbit_fields(pbit_graph g, const int8_t* spins, int32_t trials, int32
 
 /*
  * The same fields computed by the tensor-core kernel (needs a graph created
- * with PBIT_GRAPH_DENSE and trials % 32 == 0, trials <= 256 or % 256 == 0):
+ * with PBIT_GRAPH_DENSE and trials % 32 == 0, trials <= 128 or % 128 == 0):
  * J as e4m3 tiles times the spins as e4m3, FP32 accumulation, exact because
  * |J| <= 16 and every partial sum is an integer below 2^24.  DEVICE int32[n*T].
  */

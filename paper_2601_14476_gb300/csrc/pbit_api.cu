@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -125,6 +126,23 @@ struct CallBuffers {
         return PBIT_OK;
     }
 };
+
+// Resolve PBIT_KERNEL_AUTO and check a forced kernel against the shape.
+static pbit_status select_kernel(const Graph& g, int requested, int32_t T, int* out) {
+    std::string why;
+    if (requested == PBIT_KERNEL_DENSE && !dense_shape_ok(g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
+    if (requested == PBIT_KERNEL_RESIDENT && !resident_fits(g, T))
+        return fail(PBIT_E_UNSUPPORTED, "anneal: n*T too large for the shared-memory resident kernel");
+    int k = requested;
+    if (k == PBIT_KERNEL_AUTO) {
+        if (dense_shape_ok(g, T, nullptr))
+            k = PBIT_KERNEL_DENSE;
+        else
+            k = resident_fits(g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
+    }
+    *out = k;
+    return PBIT_OK;
+}
 
 static pbit_status check_device(const Graph* g) {
     int cur = -1;
@@ -308,6 +326,16 @@ void pbit_anneal_params_default(pbit_anneal_params* p) {
     p->kernel = PBIT_KERNEL_AUTO;
 }
 
+pbit_status pbit_select_kernel(pbit_graph g, int32_t requested, int32_t trials, int32_t* kernel) {
+    if (!g || !kernel || trials < 1 || requested < 0 || requested > 3)
+        return fail(PBIT_E_INVALID, "select_kernel: bad argument");
+    int k = 0;
+    pbit_status st = select_kernel(*g, requested, trials, &k);
+    if (st != PBIT_OK) return st;
+    *kernel = k;
+    return PBIT_OK;
+}
+
 pbit_status pbit_init_spins(pbit_graph g, int32_t trials, uint64_t seed, uint32_t instance, int8_t* spins,
                             void* stream) {
     if (!g || !spins || trials < 1) return fail(PBIT_E_INVALID, "init_spins: bad argument");
@@ -331,17 +359,8 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     cudaStream_t s = (cudaStream_t)p->stream;
     const int64_t cells = (int64_t)g->n * T;
 
-    int kernel = p->kernel;
-    std::string why;
-    if (kernel == PBIT_KERNEL_DENSE && !dense_shape_ok(*g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
-    if (kernel == PBIT_KERNEL_RESIDENT && !resident_fits(*g, T))
-        return fail(PBIT_E_UNSUPPORTED, "anneal: n*T too large for the shared-memory resident kernel");
-    if (kernel == PBIT_KERNEL_AUTO) {
-        if (dense_shape_ok(*g, T, nullptr))
-            kernel = PBIT_KERNEL_DENSE;
-        else
-            kernel = resident_fits(*g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
-    }
+    int kernel = 0;
+    if ((st = select_kernel(*g, p->kernel, T, &kernel)) != PBIT_OK) return st;
 
     // host-side tables
     std::vector<float> tab;
@@ -424,10 +443,24 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         if ((st = cb.alloc(&t0, tb)) != PBIT_OK) return st;
         if ((st = cb.alloc(&t1, tb)) != PBIT_OK) return st;
         PBIT_CUDA_TRY(launch_to_tiled(*g, cur, T, t0, s));
-        for (int32_t j = b; j < e; ++j) {
-            a.step = j;
-            PBIT_CUDA_TRY(launch_dense_step(*g, a, t0, t1, nullptr, g->err, s));
-            std::swap(t0, t1);
+        // persistent form when every cluster can be resident, else one launch per step
+        unsigned* done = nullptr;
+        const int RB = g->dense.n_pad / 128, TB = T <= 128 ? 1 : T / 128;
+        if ((st = cb.alloc(&done, (size_t)RB * TB)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned) * (size_t)RB * TB, s));
+        static const bool stepwise = std::getenv("PBIT_DENSE_STEPWISE") != nullptr;  // force per-step launches
+        cudaError_t pe = stepwise ? cudaErrorNotSupported
+                                  : launch_dense_persistent(*g, a, t0, t1, b, e, done, g->err, s);
+        if (pe == cudaSuccess) {
+            if ((e - b) % 2 == 1) std::swap(t0, t1);
+        } else if (pe == cudaErrorNotSupported) {
+            for (int32_t j = b; j < e; ++j) {
+                a.step = j;
+                PBIT_CUDA_TRY(launch_dense_step(*g, a, t0, t1, nullptr, g->err, s));
+                std::swap(t0, t1);
+            }
+        } else {
+            return cuda_fail(pe, "dense persistent launch");
         }
         PBIT_CUDA_TRY(launch_from_tiled(*g, t0, T, spins_out, s));
         return PBIT_OK;
@@ -502,13 +535,24 @@ static pbit_status cut_or_energy(pbit_graph g, const int8_t* spins, int32_t tria
     pbit_status st = check_device(g);
     if (st != PBIT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // tensor-core route when the graph holds the dense operand (and h = 0 for the energy)
+    const bool dense = dense_shape_ok(*g, trials, nullptr) && !(energy && g->has_h);
+    uint8_t* tiled = nullptr;
+    if (dense) PBIT_CUDA_TRY(cudaMallocAsync((void**)&tiled, dense_spin_bytes(*g, trials), s));
+    auto run = [&](int64_t* dst) -> cudaError_t {
+        return dense ? launch_dense_cut_energy(*g, spins, trials, dst, energy, tiled, s)
+                     : launch_cut_energy(*g, spins, trials, dst, energy, s);
+    };
     if (!on_host) {
-        PBIT_CUDA_TRY(launch_cut_energy(*g, spins, trials, out, energy, s));
+        cudaError_t e1 = run(out);
+        if (tiled) cudaFreeAsync(tiled, s);
+        if (e1 != cudaSuccess) return cuda_fail(e1, energy ? "energy" : "cut");
         return PBIT_OK;
     }
     int64_t* d = nullptr;
     PBIT_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(int64_t) * (size_t)trials, s));
-    cudaError_t err = launch_cut_energy(*g, spins, trials, d, energy, s);
+    cudaError_t err = run(d);
+    if (tiled) cudaFreeAsync(tiled, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(out, d, sizeof(int64_t) * (size_t)trials, cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(d, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);

@@ -6,28 +6,32 @@
 // kind::f8f6f4 with e4m3 operands and an FP32 accumulator.  It is exact here:
 // every J_ij with |J_ij| <= 16 and every spin (+-1, or 0 for padding) is an
 // e4m3 value, each product is an integer of magnitude <= 16, and every
-// partial sum is an integer below 2^14 in magnitude (K slice of 256 nodes),
+// partial sum is an integer of magnitude at most 16 * 512 = 2^13 (K slice of
+// 512 nodes),
 // far inside FP32's exact-integer range.  The K-slice partials are summed in
 // FP32 (still exact: |D| < 2^24) by a cluster reduction over distributed
 // shared memory.
 //
 // Work decomposition of one step (one launch):
 //   grid = (KS, RB, TB) CTAs, cluster = (KS, 1, 1)
-//   CTA (ks, rb, tb): rows rb*128..+128 of J, K slice ks*256..+256, trials
-//   tb*NT..+NT.  It bulk-copies its J tile (128 x 256 e4m3) and spin tile
-//   (NT x 256 e4m3) into shared memory, issues 8 tcgen05.mma (M=128, N=NT,
-//   K=32) into TMEM, reads the 128 x NT partial back, publishes it in its
+//   CTA (ks, rb, tb): rows rb*128..+128 of J, K slice ks*512..+512, trials
+//   tb*NT..+NT (NT <= 128).  It bulk-copies its J tile (128 x 512 e4m3) and
+//   spin tile (NT x 512 e4m3) into shared memory, issues 16 tcgen05.mma
+//   (M=128, N=NT, K=32) into TMEM, reads the 128 x NT partial back, publishes it in its
 //   shared memory; after a cluster barrier each CTA sums, for its NT/KS
 //   trial columns, the KS partials of its 128 rows and applies the p-bit
 //   update (Eq. pbits_variability with the timing draw) to them.
 //
 // Global layouts (both written in the exact no-swizzle K-major core-matrix
 // order the MMA reads, so one bulk copy moves a whole tile):
-//   J tiles:  [rb][ks][row group (16)][k core (16)][row (8)][16 bytes]
-//   spins:    [ks][trial group (T/8)][k core (16)][trial (8)][16 bytes]
+//   J tiles:  [rb][ks][row group (16)][k core (32)][row (8)][16 bytes]
+//   spins:    [ks][trial group (T/8)][k core (32)][trial (8)][16 bytes]
 // where a "k core" is 16 consecutive nodes j.  Core matrices are 8 x 16 B =
 // 128 contiguous bytes: leading byte offset (next core along K) = 128,
-// stride byte offset (next 8-row group) = 16 * 128 = 2048.
+// stride byte offset (next 8-row group) = 32 * 128 = 4096.
+// The K slice is 512 nodes so that a cluster has at most n/512 CTAs: with
+// one CTA per SM (about 190-230 KB of shared memory each) GB300 keeps 36
+// clusters of 4 resident but only 15 of 8.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -44,9 +48,11 @@ namespace pbit {
 namespace {
 
 constexpr int kRows = 128;          // MMA M
-constexpr int kSlice = 256;         // K slice per CTA (nodes)
+constexpr int kSlice = 512;         // K slice per CTA (nodes)
 constexpr int kCores = kSlice / 16; // k cores per slice
 constexpr int kThreads = 256;
+constexpr int kMaxNT = 128;         // trials per CTA tile (MMA N)
+constexpr int kFlagsPerSlice = kSlice / kRows;  // row blocks producing one K slice
 constexpr int kPad = 4;             // partial row padding (floats)
 constexpr uint8_t kE4m3Plus1 = 0x38, kE4m3Minus1 = 0xB8;
 
@@ -142,6 +148,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "memory");
 }
 
+// 32 lanes x 16 consecutive 32-bit columns per warp.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -160,6 +177,7 @@ struct DenseArgs {
     const uint8_t* s_in;     // tiled spins (e4m3), current state
     uint8_t* s_out;          // tiled spins, next state (unused when fields_out is set)
     int32_t* fields_out;     // if non-null: write D = h + J s as int32 [n][T] and skip the update
+    unsigned long long* obs_out;  // if non-null: add S_t = sum_i s_it (J s)_it per trial, skip the update
     const int32_t* h;
     NodeParams par;
     const float* i0_table;
@@ -174,8 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     // 128-align the dynamic shared memory base (descriptors and bulk copies need 16)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    uint8_t* sA = smem;                                   // 128 x 256 bytes
-    uint8_t* sB = sA + kRows * kSlice;                    // NT x 256 bytes
+    uint8_t* sA = smem;                                   // 128 x kSlice bytes
+    uint8_t* sB = sA + kRows * kSlice;                    // NT x kSlice bytes
     float* part = (float*)(sB + (size_t)a.NT * kSlice);   // 128 x (NT + kPad)
     uint64_t* bars = (uint64_t*)(part + (size_t)kRows * (a.NT + kPad));
     uint32_t* tmem_slot = (uint32_t*)(bars + 2);
@@ -193,17 +211,20 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();  // the CTA barrier below is warp-aligned: reconverge first
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // ---- load the J tile and the spin tile, run the MMAs
+    // ---- load the J tile and the spin tile, run the MMAs (lane 0 of warp 0)
     if (tid == 0) {
         const uint32_t bytesA = kRows * kSlice, bytesB = (uint32_t)NT * kSlice;
         mbar_expect_tx(&bars[0], bytesA + bytesB);
@@ -228,6 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
             mma_commit(&bars[1]);
         }
     }
+    __syncwarp();
     // thread 0 waits (bounded) for the MMA results and broadcasts the outcome,
     // so the warp-collective TMEM loads below are taken uniformly
     __shared__ int s_ok;
@@ -238,17 +260,19 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
         }
         s_ok = ok ? 1 : 0;
     }
+    __syncwarp();
     __syncthreads();
     ok = s_ok != 0;
     tc_fence_after();
 
-    // ---- TMEM -> shared partial (warps 0-3: columns [0,128), warps 4-7: [128,256))
+    // ---- TMEM -> shared partial: warp w reads lanes 32*(w%4).., 32-column chunks w/4, w/4+2, ...
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
     const int stride = NT + kPad;
     if (ok) {
-        for (int c0 = (warp >> 2) * 128; c0 < NT; c0 += 256) {
-            for (int cc = c0; cc < min(NT, c0 + 128); cc += 32) {
+        for (int ch = warp >> 2; ch < NT / 32; ch += 2) {
+            {
+                const int cc = ch * 32;
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cc, v);
                 tmem_wait_ld();
@@ -280,15 +304,31 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
     const int cb = 2 * (half == 0 ? pb : pm), ce = 2 * (half == 0 ? pm : pe);
     const bool active = ok && i < a.n;
     const int hi = (active && a.h) ? a.h[i] : 0;
-    const float I0 = a.fields_out ? 0.0f : a.i0_table[a.step];
+    const float I0 = (a.fields_out || a.obs_out) ? 0.0f : a.i0_table[a.step];
     const float lam = (active && a.par.lambda) ? a.par.lambda[i] : 1.0f;
     const float del = (active && a.par.delta) ? a.par.delta[i] : 0.0f;
     const uint32_t thr = (active && a.par.thr) ? a.par.thr[i] : (1u << 24);
-    for (int c = cb; active && c < ce; c += 16) {
+    for (int c = cb; c < ce; c += 16) {
         const int cnt = min(16, ce - c);
         float acc[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+        if (a.obs_out) {
+            // per-trial S_t: every lane of a warp takes part in the warp sums (zeros where inactive)
+            for (int src = 0; active && src < a.KS; ++src) {
+                const float* rp = cluster.map_shared_rank(part, src) + (size_t)r * stride + c;
+                for (int q = 0; q < cnt; ++q) acc[q] += rp[q];
+            }
+            for (int q = 0; q < cnt; ++q) {
+                const int t = tb * NT + c + q;
+                int v = 0;
+                if (active) v = (a.s_in[spin_off(t, i, a.T)] == kE4m3Plus1 ? 1 : -1) * __float2int_rn(acc[q]);
+                v = __reduce_add_sync(0xFFFFFFFFu, v);
+                if (lane == 0 && v != 0) atomicAdd(a.obs_out + t, (unsigned long long)(long long)v);
+            }
+            continue;
+        }
+        if (!active) continue;
         for (int src = 0; src < a.KS; ++src) {
             const float* rp = cluster.map_shared_rank(part, src) + (size_t)r * stride + c;
             if (cnt == 16 && (c & 3) == 0) {
@@ -330,6 +370,272 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
     cluster.sync();  // peers leave only after every CTA has read their partials
 }
 
+// ------------------------------------------------------------------------
+// Persistent form: one launch runs steps [b, e).  Each CTA loads its J tile
+// once and keeps it in shared memory; per step it waits (bounded) until the
+// two clusters that produce its K slice have published the previous step,
+// bulk-copies its spin tile, runs the MMAs, and the cluster reduces and
+// updates as above.  Progress is published per cluster in `done`.  All
+// clusters must be co-resident (checked on the host before launch).
+// ------------------------------------------------------------------------
+struct PersistArgs {
+    DenseArgs d;
+    uint8_t* buf0;
+    uint8_t* buf1;
+    int32_t step_begin, step_end;
+    unsigned* done;   // [RB * TB], zero on entry
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Warps 0..15 read TMEM and run the epilogue; warp 16 is the control warp
+// that waits for the producers, issues the bulk copy and the MMAs.
+constexpr int kEpi = 512;                      // epilogue threads
+constexpr int kPersistThreads = kEpi + 32;
+constexpr int kMaxItems = 4;                   // (NT/2/KS) pairs x 32 row quads <= 4 x 512
+
+// 17 warps share 4 SM sub-partitions (one holds 5 warps and 16K registers),
+// so the compiler keeps this kernel near 100 registers per thread.
+__global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(PersistArgs pa) {
+    const DenseArgs& a = pa.d;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    const int NT = a.NT;
+    uint8_t* sA = smem;                                    // 128 x kSlice bytes, stationary
+    uint8_t* sB = sA + kRows * kSlice;                     // NT x kSlice bytes
+    float* part = (float*)(sB + (size_t)NT * kSlice);      // column-major [NT][128]
+    float* s_lam = part + (size_t)NT * kRows;              // per-row parameters
+    float* s_del = s_lam + kRows;
+    uint32_t* s_thr = (uint32_t*)(s_del + kRows);
+    int32_t* s_h = (int32_t*)(s_thr + kRows);
+    uint4* s_rw = (uint4*)(s_h + kRows);                   // Philox words [4][kEpi] of the first item
+    uint64_t* bars = (uint64_t*)(s_rw + 4 * kEpi);         // 0: J, 1: spins, 2: MMA
+    uint32_t* tmem_slot = (uint32_t*)(bars + 3);
+    __shared__ int s_abort;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int ks = blockIdx.x, rb = blockIdx.y, tb = blockIdx.z;
+    const int RB = gridDim.y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool control = warp == kEpi / 32;
+    const uint32_t ncols = NT <= 32 ? 32 : (NT <= 64 ? 64 : 128);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (control) {
+        if (lane == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            mbar_init(&bars[2], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            s_abort = 0;
+        }
+        __syncwarp();
+    }
+    // per-row parameters staged in shared memory
+    for (int r = tid; r < kRows; r += kPersistThreads) {
+        const int i = rb * kRows + r;
+        const bool in = i < a.n;
+        s_lam[r] = (in && a.par.lambda) ? a.par.lambda[i] : 1.0f;
+        s_del[r] = (in && a.par.delta) ? a.par.delta[i] : 0.0f;
+        s_thr[r] = (in && a.par.thr) ? a.par.thr[i] : (1u << 24);
+        s_h[r] = (in && a.h) ? a.h[i] : 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (control) {
+        if (lane == 0) {
+            mbar_expect_tx(&bars[0], kRows * kSlice);
+            bulk_g2s(sA, a.Jt + ((size_t)rb * a.KS + ks) * (size_t)(kRows * kSlice), kRows * kSlice, &bars[0]);
+            if (!mbar_wait_bounded(&bars[0], 0)) {
+                atomicExch(a.err, 1);
+                s_abort = 1;
+            }
+        }
+        __syncwarp();
+    }
+    const int pairs = NT / 2;
+    const int pb = (ks * pairs) / a.KS, pe = ((ks + 1) * pairs) / a.KS;
+    const int items = (pe - pb) * (kRows / 4);
+    const unsigned* prod0 = pa.done + (size_t)tb * RB + (size_t)kFlagsPerSlice * ks;
+    const uint32_t idesc = idesc_e4m3((uint32_t)NT);
+    const int L = pa.step_end - pa.step_begin;
+    // Item `it` = (pair pb + it/32, rows 4*(it%32)..+4).  The thread that
+    // writes an item's new spins at step s reads them as old spins at s+1, so
+    // they stay in registers between steps.
+    uint32_t prev0[kMaxItems], prev1[kMaxItems];
+
+    for (int ls = 0; ls < L; ++ls) {
+        const int step = pa.step_begin + ls;
+        const uint8_t* cur = (ls & 1) ? pa.buf1 : pa.buf0;
+        uint8_t* nxt = (ls & 1) ? pa.buf0 : pa.buf1;
+        if (control) {
+            if (lane == 0 && !s_abort) {
+                bool ok = true;
+                if (ls > 0) {
+                    const long long start = clock64();
+                    for (int f = 0; f < kFlagsPerSlice && ok; ++f) {
+                        while (ld_acquire(prod0 + f) < (unsigned)ls) {
+                            if (clock64() - start > (1ll << 31)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                    }
+                    fence_proxy_async();
+                }
+                if (ok) {
+                    mbar_expect_tx(&bars[1], (uint32_t)NT * kSlice);
+                    bulk_g2s(sB, cur + (size_t)ks * ((size_t)a.T * kSlice) + (size_t)tb * NT * kSlice,
+                             (uint32_t)NT * kSlice, &bars[1]);
+                    ok = mbar_wait_bounded(&bars[1], (uint32_t)(ls & 1));
+                }
+                if (ok) {
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+                    for (int kk = 0; kk < kSlice / 32; ++kk)
+                        mma_e4m3(tmem, smem_desc(a0 + kk * 256, 128, kCores * 128),
+                                 smem_desc(b0 + kk * 256, 128, kCores * 128), idesc, kk > 0 ? 1u : 0u);
+                    mma_commit(&bars[2]);
+                    ok = mbar_wait_bounded(&bars[2], (uint32_t)(ls & 1));
+                }
+                if (!ok) {
+                    atomicExch(a.err, 3);
+                    s_abort = 1;
+                }
+            }
+            __syncwarp();  // reconverge before the warp-aligned CTA barrier
+        } else if (tid < items) {
+            // this thread's Philox words for the step, drawn while the control warp waits
+            const int p = pb + (tid >> 5);
+            const int t0 = tb * NT + 2 * p;
+            const int i0 = rb * kRows + (tid & 31) * 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                s_rw[k * kEpi + tid] = philox((uint32_t)(i0 + k), (uint32_t)step, (uint32_t)t0 >> 1, a.instance,
+                                              a.seed_lo, a.seed_hi);
+            if (ls == 0) {
+#pragma unroll
+                for (int slot = 0; slot < kMaxItems; ++slot) {
+                    const int it = tid + slot * kEpi;
+                    if (it < items) {
+                        const int tt = tb * NT + 2 * (pb + (it >> 5));
+                        const int ii = rb * kRows + (it & 31) * 4;
+                        prev0[slot] = *reinterpret_cast<const uint32_t*>(cur + spin_off(tt, ii, a.T));
+                        prev1[slot] = *reinterpret_cast<const uint32_t*>(cur + spin_off(tt + 1, ii, a.T));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const bool abort = s_abort != 0;
+        tc_fence_after();
+        if (!abort && !control) {
+            // TMEM -> column-major partial: lane = row, 32-column chunks over the four warp groups
+            const int quarter = warp & 3;
+            const int row = quarter * 32 + lane;
+            for (int ch = warp >> 2; ch < NT / 16; ch += 4) {
+                const int c = ch * 16;
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) part[(size_t)(c + q) * kRows + row] = __uint_as_float(v[q]);
+            }
+        }
+        tc_fence_before();
+        cluster.sync();
+        if (!abort && !control) {
+            const float I0 = a.i0_table[step];
+#pragma unroll
+            for (int slot = 0; slot < kMaxItems; ++slot) {
+                const int it = tid + slot * kEpi;
+                if (it < items) {
+                    const int r0 = (it & 31) * 4;
+                    const int lc0 = 2 * (pb + (it >> 5));
+                    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+                    for (int src = 0; src < a.KS; ++src) {
+                        const float* rp = cluster.map_shared_rank(part, src);
+                        const float4 x = *reinterpret_cast<const float4*>(rp + (size_t)lc0 * kRows + r0);
+                        const float4 y = *reinterpret_cast<const float4*>(rp + (size_t)(lc0 + 1) * kRows + r0);
+                        acc0.x += x.x; acc0.y += x.y; acc0.z += x.z; acc0.w += x.w;
+                        acc1.x += y.x; acc1.y += y.y; acc1.z += y.z; acc1.w += y.w;
+                    }
+                    const float f0[4] = {acc0.x, acc0.y, acc0.z, acc0.w};
+                    const float f1[4] = {acc1.x, acc1.y, acc1.z, acc1.w};
+                    const int t0 = tb * NT + lc0;
+                    const int i0 = rb * kRows + r0;
+                    const uint32_t old0 = prev0[slot], old1 = prev1[slot];
+                    uint32_t n0 = 0u, n1 = 0u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = i0 + k;
+                        if (i < a.n) {
+                            const int r = r0 + k;
+                            const uint4 rw = slot == 0 ? s_rw[k * kEpi + tid]
+                                                       : philox((uint32_t)i, (uint32_t)step, (uint32_t)t0 >> 1,
+                                                                a.instance, a.seed_lo, a.seed_hi);
+                            const float lam = s_lam[r], del = s_del[r];
+                            const uint32_t thr = s_thr[r];
+                            const int D0 = s_h[r] + __float2int_rn(f0[k]);
+                            const int D1 = s_h[r] + __float2int_rn(f1[k]);
+                            const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, D0));
+                            const uint32_t k1 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, D1));
+                            const int s0 = pbit_next(rw.x, rw.y, k0, thr, ((old0 >> (8 * k)) & 0xFF) == kE4m3Plus1 ? 1 : -1);
+                            const int s1 = pbit_next(rw.z, rw.w, k1, thr, ((old1 >> (8 * k)) & 0xFF) == kE4m3Plus1 ? 1 : -1);
+                            n0 |= (uint32_t)(s0 > 0 ? kE4m3Plus1 : kE4m3Minus1) << (8 * k);
+                            n1 |= (uint32_t)(s1 > 0 ? kE4m3Plus1 : kE4m3Minus1) << (8 * k);
+                        }
+                    }
+                    prev0[slot] = n0;
+                    prev1[slot] = n1;
+                    *reinterpret_cast<uint32_t*>(nxt + spin_off(t0, i0, a.T)) = n0;
+                    *reinterpret_cast<uint32_t*>(nxt + spin_off(t0 + 1, i0, a.T)) = n1;
+                }
+            }
+        }
+        // The cluster barrier orders every CTA's spin stores before the
+        // control thread of rank 0 publishes them device-wide.
+        cluster.sync();
+        if (control) {
+            if (lane == 0 && cluster.block_rank() == 0) {
+                __threadfence();
+                fence_proxy_async();
+                st_release(pa.done + (size_t)tb * RB + rb, (unsigned)(ls + 1));
+            }
+            __syncwarp();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+size_t persist_smem_bytes(int NT) {
+    return 128 + (size_t)kRows * kSlice + (size_t)NT * kSlice + (size_t)NT * kRows * sizeof(float) +
+           (size_t)kRows * 16 + (size_t)4 * kEpi * sizeof(uint4) + 64;
+}
+
 // int8 trial-major [n][T]  <->  tiled e4m3 (padding nodes written as 0)
 __global__ void to_tiled_kernel(const int8_t* __restrict__ s, int32_t n, int32_t n_pad, int32_t T,
                                 uint8_t* __restrict__ out) {
@@ -352,6 +658,12 @@ __global__ void from_tiled_kernel(const uint8_t* __restrict__ in, int32_t n, int
     }
 }
 
+// cut_t = (S_t + 2W)/4 and H_t = -S_t/2 (h = 0) from S_t = sum_i s_it (J s)_it.
+__global__ void finish_dense_observe(long long* v, int32_t T, long long two_w, int energy) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T) v[t] = energy ? -(v[t] / 2) : (v[t] + two_w) / 4;
+}
+
 size_t dense_smem_bytes(int NT) {
     return 128 + (size_t)kRows * kSlice + (size_t)NT * kSlice + (size_t)kRows * (NT + kPad) * sizeof(float) + 64;
 }
@@ -372,11 +684,11 @@ uint8_t e4m3_of_int(int v) {
 // ------------------------------------------------------------- host side ----
 bool dense_shape_ok(const Graph& g, int32_t T, std::string* why) {
     if (!g.dense.J_e4m3) {
-        if (why) *why = "graph was created without PBIT_GRAPH_DENSE (or |w| > 16 / n > 4096)";
+        if (why) *why = "graph was created without PBIT_GRAPH_DENSE";
         return false;
     }
-    if (T % 32 != 0 || (T > 256 && T % 256 != 0)) {
-        if (why) *why = "dense kernel needs trials % 32 == 0 and (trials <= 256 or trials % 256 == 0)";
+    if (T % 32 != 0 || (T > kMaxNT && T % kMaxNT != 0)) {
+        if (why) *why = "dense kernel needs trials % 32 == 0 and (trials <= 128 or trials % 128 == 0)";
         return false;
     }
     return true;
@@ -385,7 +697,7 @@ bool dense_shape_ok(const Graph& g, int32_t T, std::string* why) {
 pbit_status build_dense_operand(Graph& g) {
     const int n_pad = ((g.n + kSlice - 1) / kSlice) * kSlice;
     const int KS = n_pad / kSlice, RB = n_pad / kRows;
-    if (KS > 16) return fail(PBIT_E_INVALID, "dense operand: n > 4096 is not supported by the tensor-core path");
+    if (KS > 16) return fail(PBIT_E_INVALID, "dense operand: n > 8192 is not supported by the tensor-core path");
     for (size_t k = 0; k < g.h_J.size() && k < (size_t)g.nnz; ++k)
         if (g.h_J[k] > 16 || g.h_J[k] < -16)
             return fail(PBIT_E_INVALID, "dense operand: |w| > 16 is not exact in e4m3");
@@ -426,19 +738,20 @@ cudaError_t launch_from_tiled(const Graph& g, const uint8_t* in, int32_t T, int8
 }
 
 cudaError_t launch_dense_step(const Graph& g, const StepArgs& sa, const uint8_t* tin, uint8_t* tout,
-                              int32_t* fields_out, int* err, cudaStream_t st) {
+                              int32_t* fields_out, int* err, cudaStream_t st, unsigned long long* obs_out) {
     DenseArgs a{};
     a.Jt = g.dense.J_e4m3;
     a.s_in = tin;
     a.s_out = tout;
     a.fields_out = fields_out;
+    a.obs_out = obs_out;
     a.h = g.h;
     a.par = sa.par;
     a.i0_table = sa.i0_table;
     a.step = sa.step;
     a.n = g.n;
     a.T = sa.T;
-    a.NT = sa.T <= 256 ? sa.T : 256;
+    a.NT = sa.T <= kMaxNT ? sa.T : kMaxNT;
     a.KS = g.dense.n_pad / kSlice;
     a.seed_lo = sa.seed_lo;
     a.seed_hi = sa.seed_hi;
@@ -467,6 +780,76 @@ cudaError_t launch_dense_step(const Graph& g, const StepArgs& sa, const uint8_t*
     e = cudaLaunchKernelEx(&cfg, dense_step_kernel, a);
     count_launches(1);
     return e;
+}
+
+// Persistent launch over steps [b, e): returns cudaErrorNotSupported (nothing
+// launched) when the clusters cannot all be resident at once.
+cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t* buf0, uint8_t* buf1, int32_t b,
+                                    int32_t e, unsigned* done, int* err, cudaStream_t st) {
+    PersistArgs pa{};
+    DenseArgs& a = pa.d;
+    a.Jt = g.dense.J_e4m3;
+    a.h = g.h;
+    a.par = sa.par;
+    a.i0_table = sa.i0_table;
+    a.n = g.n;
+    a.T = sa.T;
+    a.NT = sa.T <= kMaxNT ? sa.T : kMaxNT;
+    a.KS = g.dense.n_pad / kSlice;
+    a.seed_lo = sa.seed_lo;
+    a.seed_hi = sa.seed_hi;
+    a.instance = sa.instance;
+    a.offset_mode = sa.offset_mode;
+    a.err = err;
+    pa.buf0 = buf0;
+    pa.buf1 = buf1;
+    pa.step_begin = b;
+    pa.step_end = e;
+    pa.done = done;
+    const size_t smem = persist_smem_bytes(a.NT);
+    cudaError_t ce = cudaFuncSetAttribute(dense_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (ce != cudaSuccess) return ce;
+    if (a.KS > 8) {
+        ce = cudaFuncSetAttribute(dense_persistent_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (ce != cudaSuccess) return ce;
+    }
+    cudaLaunchConfig_t cfg{};
+    const int RB = g.dense.n_pad / kRows, TB = sa.T / a.NT;
+    cfg.gridDim = dim3((unsigned)a.KS, (unsigned)RB, (unsigned)TB);
+    cfg.blockDim = dim3(kPersistThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.KS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int max_clusters = 0;
+    ce = cudaOccupancyMaxActiveClusters(&max_clusters, dense_persistent_kernel, &cfg);
+    if (ce != cudaSuccess) return ce;
+    if (max_clusters < RB * TB) return cudaErrorNotSupported;
+    ce = cudaLaunchKernelEx(&cfg, dense_persistent_kernel, pa);
+    count_launches(1);
+    return ce;
+}
+
+cudaError_t launch_dense_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
+                                    uint8_t* tiled_scratch, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t) * (size_t)T, st);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_to_tiled(g, spins, T, tiled_scratch, st)) != cudaSuccess) return e;
+    StepArgs sa{};
+    sa.T = T;
+    if ((e = launch_dense_step(g, sa, tiled_scratch, nullptr, nullptr, g.err, st,
+                               reinterpret_cast<unsigned long long*>(out))) != cudaSuccess)
+        return e;
+    finish_dense_observe<<<(T + 255) / 256, 256, 0, st>>>(reinterpret_cast<long long*>(out), T,
+                                                           2 * (long long)g.total_weight, energy ? 1 : 0);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace pbit

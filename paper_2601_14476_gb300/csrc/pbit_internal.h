@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pbit.h"
+#include "pbit.h"
 
 namespace pbit {
 
@@ -103,7 +103,13 @@ size_t dense_spin_bytes(const Graph& g, int32_t T);
 cudaError_t launch_to_tiled(const Graph& g, const int8_t* s, int32_t T, uint8_t* out, cudaStream_t st);
 cudaError_t launch_from_tiled(const Graph& g, const uint8_t* in, int32_t T, int8_t* s, cudaStream_t st);
 cudaError_t launch_dense_step(const Graph& g, const StepArgs& sa, const uint8_t* tin, uint8_t* tout,
-                              int32_t* fields_out, int* err, cudaStream_t st);
+                              int32_t* fields_out, int* err, cudaStream_t st,
+                              unsigned long long* obs_out = nullptr);
+// exact cut (energy when h = 0) through the tensor-core fields; needs n_pad*T bytes of scratch
+cudaError_t launch_dense_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
+                                    uint8_t* tiled_scratch, cudaStream_t st);
+cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t* buf0, uint8_t* buf1, int32_t b,
+                                    int32_t e, unsigned* done, int* err, cudaStream_t st);
 // resident single-CTA anneal: all steps in one launch, spins in shared memory
 bool resident_fits(const Graph& g, int32_t T);
 cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,

@@ -77,6 +77,7 @@ def _declare(lib):
         "pbit_anneal": ([_P, _P, _P, _P], C.c_int),
         "pbit_anneal_noalloc": ([_P, _P, _P, _P], C.c_int),
         "pbit_init_spins": ([_P, i32, u64, u32, _P, _P], C.c_int),
+        "pbit_select_kernel": ([_P, i32, i32, _P], C.c_int),
         "pbit_fields": ([_P, _P, i32, _P, _P], C.c_int),
         "pbit_fields_dense": ([_P, _P, i32, _P, _P], C.c_int),
         "pbit_graph_status": ([_P, _P], C.c_int),
@@ -222,6 +223,12 @@ def pbit_anneal(g, params, spins_in, spins_out):
 def pbit_anneal_noalloc(g, params, spins_in, spins_out):
     """pbit_anneal with its scratch in the library's fixed device array (no allocation)."""
     _check(lib().pbit_anneal_noalloc(g, C.byref(params), _dev(spins_in), _dev(spins_out)))
+
+
+def pbit_select_kernel(g, requested, trials) -> int:
+    out = C.c_int32()
+    _check(lib().pbit_select_kernel(g, int(requested), int(trials), C.byref(out)))
+    return out.value
 
 
 def pbit_init_spins(g, trials, seed, instance, spins, stream=None):

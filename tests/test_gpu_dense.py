@@ -144,3 +144,57 @@ def test_dense_full_size_sampled():
     assert not bad.any() or np.abs(gap[bad]).max() < BAND
     assert np.array_equal(G.cut(nxt), oracle.cut(g.src, g.dst, g.w, n_host))
     G.status()
+
+
+def test_dense_persistent_equals_stepwise(tmp_path):
+    """The persistent tensor-core kernel equals one launch per step (forced in a child process)."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2601_14476_gb300 import inputs, pbit\n"
+        "g = inputs.complete_pm1(700, 5)\n"
+        "var = inputs.variability(700, 5)\n"
+        "G = pbit.Graph.from_inputs(g, dense=True)\n"
+        "l0 = pbit.pbit_launch_count()\n"
+        "out = G.anneal(128, 77, seed=4, variability=var, kernel=pbit.KERNEL_DENSE)\n"
+        "torch.cuda.synchronize(); G.status()\n"
+        "launches = pbit.pbit_launch_count() - l0\n"
+        "import os\n"
+        "assert (launches > 77) if os.environ.get('PBIT_DENSE_STEPWISE') else (launches < 8), launches\n"
+        "np.save(%r, out.cpu().numpy())\n")
+    outs = []
+    for k, env_extra in enumerate(({}, {"PBIT_DENSE_STEPWISE": "1"})):
+        path = str(tmp_path / f"o{k}.npy")
+        env = dict(os.environ, **env_extra)
+        subprocess.run([sys.executable, "-c", code % path], check=True, env=env, timeout=300)
+        outs.append(np.load(path))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_select_kernel():
+    g = _complete(300, 1)
+    G = pbit.Graph.from_inputs(g, dense=True)
+    assert pbit.pbit_select_kernel(G.handle, pbit.KERNEL_AUTO, 64) == pbit.KERNEL_DENSE
+    assert pbit.pbit_select_kernel(G.handle, pbit.KERNEL_AUTO, 48) in (pbit.KERNEL_RESIDENT, pbit.KERNEL_SPARSE)
+    S = pbit.Graph.from_inputs(inputs.torus_2d(100, 200, 1))
+    assert pbit.pbit_select_kernel(S.handle, pbit.KERNEL_AUTO, 1024) == pbit.KERNEL_SPARSE
+
+
+@pytest.mark.parametrize("n,T", [(300, 64), (2000, 256), (1100, 96)])
+def test_dense_cut_energy_match_oracle(n, T):
+    """pbit_cut / pbit_energy take the tensor-core route on dense graphs; both are exact."""
+    g = _complete(n, 21)
+    G = pbit.Graph.from_inputs(g, dense=True)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    s = inputs.random_spins(n, T, 8)
+    d = _dev(s)
+    assert np.array_equal(G.cut(d), oracle.cut(g.src, g.dst, g.w, s))
+    assert np.array_equal(G.energy(d), oracle.energy(csr, s))
+    # with biases the energy goes through the CSR kernel
+    h = np.random.default_rng(3).integers(-9, 10, n).astype(np.int32)
+    Gh = pbit.Graph(g.n, g.src, g.dst, g.w, h=h, dense=True)
+    assert np.array_equal(Gh.energy(d), oracle.energy(csr, s, h))
+    assert np.array_equal(Gh.cut(d), oracle.cut(g.src, g.dst, g.w, s))
+    G.status()
