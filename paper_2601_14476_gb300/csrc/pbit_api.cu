@@ -97,6 +97,8 @@ static void release(Graph* g) {
     cudaFree(g->h);
     cudaFree(g->dense.J_e4m3);
     cudaFree(g->err);
+    cudaFree(g->wabs);
+    cudaFree(g->tab_off);
     cudaSetDevice(cur);
 }
 
@@ -215,6 +217,21 @@ static pbit_status build_host(Graph& g, int32_t n, int64_t n_edges, const int32_
         max_field = std::max(max_field, absum + hi);
     }
     if (max_field >= (1 << 24)) return fail(PBIT_E_INVALID, "graph: |field| could reach 2^24");
+    // per-node field half-width W_i and threshold-table offsets
+    g.h_wabs.assign((size_t)n, 0);
+    g.h_tab_off.assign((size_t)n + 1, 0);
+    int64_t acc_off = 0;
+    g.max_wabs = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t W = 0;
+        for (int32_t k = g.h_row_ptr[(size_t)i]; k < g.h_row_ptr[(size_t)i + 1]; ++k) W += std::abs((int32_t)g.h_J[(size_t)k]);
+        g.h_wabs[(size_t)i] = W;
+        g.max_wabs = std::max(g.max_wabs, W);
+        g.h_tab_off[(size_t)i] = (int32_t)std::min<int64_t>(acc_off, INT32_MAX);
+        acc_off += (int64_t)W + 1;
+    }
+    g.tab_ok = acc_off < INT32_MAX;
+    g.h_tab_off[(size_t)n] = (int32_t)std::min<int64_t>(acc_off, INT32_MAX);
     g.max_abs_field = (int32_t)max_field;
     g.has_h = h != nullptr;
     if (h) g.h_h.assign(h, h + n);
@@ -247,6 +264,8 @@ pbit_status pbit_graph_create(int32_t n, int64_t n_edges, const int32_t* src, co
     if ((st = upload(&g->col, g->h_col.data(), (size_t)g->nnz, g->device_bytes)) != PBIT_OK) goto err;
     if ((st = upload(&g->J, g->h_J.data(), (size_t)g->nnz, g->device_bytes)) != PBIT_OK) goto err;
     if (h && (st = upload(&g->h, h, (size_t)n, g->device_bytes)) != PBIT_OK) goto err;
+    if ((st = upload(&g->wabs, g->h_wabs.data(), (size_t)n, g->device_bytes)) != PBIT_OK) goto err;
+    if ((st = upload(&g->tab_off, g->h_tab_off.data(), (size_t)n + 1, g->device_bytes)) != PBIT_OK) goto err;
     if ((st = upload(&g->err, (const int*)nullptr, 1, g->device_bytes)) != PBIT_OK) goto err;
     {
         cudaError_t ce = cudaMemset(g->err, 0, sizeof(int));
@@ -388,6 +407,8 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     a.col = g->col;
     a.J = g->J;
     a.h = g->h;
+    a.wabs = g->wabs;
+    a.tab_off = g->tab_off;
     a.n = g->n;
     a.T = T;
     a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
@@ -476,12 +497,13 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         PBIT_CUDA_TRY(cudaMemcpyAsync(scratch, cur, (size_t)cells, cudaMemcpyDeviceToDevice, s));
         cur = scratch;
     }
+    const SparseVariant variant = choose_sparse_variant(*g, T);
     for (int32_t j = 0; j < k; ++j) {
         int8_t* dst = ((k - 1 - j) % 2 == 0) ? spins_out : scratch;
         a.step = b + j;
         a.in = cur;
         a.out = dst;
-        PBIT_CUDA_TRY(launch_sparse_step(a, s));
+        PBIT_CUDA_TRY(launch_sparse_step(a, s, variant));
         cur = dst;
     }
     return PBIT_OK;

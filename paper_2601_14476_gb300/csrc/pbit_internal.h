@@ -51,6 +51,10 @@ struct Graph {
     int32_t* col = nullptr;       // [nnz]
     int8_t* J = nullptr;          // [nnz]
     int32_t* h = nullptr;         // [n] or null
+    int32_t* wabs = nullptr;      // [n] W_i = sum_j |J_ij|: the field of node i lies in h_i + [-W_i, W_i]
+    int32_t* tab_off = nullptr;   // [n+1] prefix sums of (W_i + 1): threshold-table offsets
+    int32_t max_wabs = 0;
+    bool tab_ok = false;          // prefix sums fit int32
     DenseOperand dense;
     int* err = nullptr;           // device word: nonzero after a bounded wait gave up
     size_t device_bytes = 0;
@@ -58,6 +62,7 @@ struct Graph {
     std::vector<int32_t> h_row_ptr, h_col;
     std::vector<int8_t> h_J;
     std::vector<int32_t> h_h;
+    std::vector<int32_t> h_wabs, h_tab_off;
     std::mutex mu;
 };
 
@@ -78,6 +83,8 @@ struct StepArgs {
     const int32_t* col;
     const int8_t* J;
     const int32_t* h;
+    const int32_t* wabs;
+    const int32_t* tab_off;
     NodeParams par;
     const float* i0_table;
     int32_t step;
@@ -92,7 +99,15 @@ struct StepArgs {
 // kernels (pbit_sparse.cu)
 cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* spins,
                               cudaStream_t s);
-cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s);
+// Sparse step with the kernel variant chosen for the graph: packed counting
+// for +-1 weights (degree <= 127) and a per-block shared-memory table of
+// decision thresholds when the node fields take few values.
+struct SparseVariant {
+    bool unit = false;
+    bool table = false;
+};
+SparseVariant choose_sparse_variant(const Graph& g, int32_t T);
+cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v = SparseVariant());
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
 cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
                               cudaStream_t s);

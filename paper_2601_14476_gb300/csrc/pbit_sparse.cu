@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "pbit_device.cuh"
 #include "pbit_internal.h"
@@ -116,28 +117,134 @@ __global__ void init_spins_kernel(int32_t n, int32_t T, uint32_t k0, uint32_t k1
 }
 
 // ------------------------------------------------------------------ step ----
-template <int G>
+// One thread per (node i, group of G trials); 256-thread blocks cover a
+// contiguous range of nodes.
+//
+// UNIT (every |J| = 1, degree <= 127): the gather counts, per trial byte,
+// the neighbours whose product J_ij * s_j is -1.  A spin byte is 0x01 (+1)
+// or 0xFF (-1), so (byte & 2) is 2 exactly for -1; XOR with 2 when J = -1
+// flips it.  Byte lanes of one 32-bit word add without carries (2 * 127 <
+// 256), and sum_j J_ij s_j = deg - 2 * count.
+//
+// TABLE: the field of node i lies in h_i + [-W_i, W_i] with the parity of
+// W_i (W_i = sum_j |J_ij|), so for this step the block first evaluates the
+// decision threshold for each of the W_i + 1 possible fields of its nodes
+// into shared memory; each update then reads its threshold by index
+// (D - h_i + W_i) / 2.  The table entries are computed by the same function
+// as the direct path, so both give identical decisions.
+constexpr int kTabMax = 4096;  // threshold entries per block (16 KB)
+
+template <int G, bool UNIT, bool TABLE>
 __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
     const int groups = a.T / G;
-    const int64_t tid = blockIdx.x * (int64_t)kBlock + threadIdx.x;
-    if (tid >= (int64_t)a.n * groups) return;
+    const int64_t total = (int64_t)a.n * groups;
+    const int64_t first = blockIdx.x * (int64_t)kBlock;
+    const int64_t tid = first + threadIdx.x;
+    const float I0 = __ldg(a.i0_table + a.step);
+    __shared__ uint32_t s_tab[TABLE ? kTabMax : 1];
+    int tab_base = 0, i_first = 0;
+    if constexpr (TABLE) {
+        i_first = (int)(first / groups);
+        const int i_last = (int)(min(total - 1, first + kBlock - 1) / groups);
+        tab_base = __ldg(a.tab_off + i_first);
+        const int cnt = __ldg(a.tab_off + i_last + 1) - tab_base;
+        for (int e = threadIdx.x; e < cnt; e += kBlock) {
+            // node of entry e: the last i in [i_first, i_last] with tab_off[i] - base <= e
+            int lo = i_first, hi = i_last;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.tab_off + mid) - tab_base <= e) lo = mid; else hi = mid - 1;
+            }
+            const int node = lo;
+            const int idx = e - (__ldg(a.tab_off + node) - tab_base);
+            const int W = __ldg(a.wabs + node);
+            const int hi_n = a.h ? __ldg(a.h + node) : 0;
+            const float lam = a.par.lambda ? __ldg(a.par.lambda + node) : 1.0f;
+            const float del = a.par.delta ? __ldg(a.par.delta + node) : 0.0f;
+            s_tab[e] = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi_n - W + 2 * idx));
+        }
+        __syncthreads();
+    }
+    if (tid >= total) return;
     const int i = (int)(tid / groups);
     const int t0 = (int)(tid - (int64_t)i * groups) * G;
-    int acc[G];
-    gather_field<G>(a.row_ptr, a.col, a.J, a.in, a.T, i, t0, acc);
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+
+    int D[G];  // exact fields, h included
+    if constexpr (UNIT && G >= 4) {
+        uint32_t cnt2[Pack<G>::W];
+#pragma unroll
+        for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] = 0;
+        for (int e = rb; e < re; ++e) {
+            const int j = __ldg(a.col + e);
+            const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
+            uint32_t v[Pack<G>::W];
+            load_group<G>(a.in + (size_t)j * a.T + t0, v);
+#pragma unroll
+            for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] += (v[w] & 0x02020202u) ^ flip;
+        }
+        const int deg = re - rb;
+#pragma unroll
+        for (int k = 0; k < G; ++k) D[k] = hi + deg - (int)((cnt2[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+    } else {
+        int acc[G];
+        gather_field<G>(a.row_ptr, a.col, a.J, a.in, a.T, i, t0, acc);
+#pragma unroll
+        for (int k = 0; k < G; ++k) D[k] = hi + acc[k];
+    }
+    int tab_off_i = 0, W_i = 0;
+    if constexpr (TABLE) {
+        tab_off_i = __ldg(a.tab_off + i) - tab_base;
+        W_i = __ldg(a.wabs + i);
+    }
+    auto kthr_of = [&](int Dk) -> uint32_t {
+        if constexpr (TABLE) return s_tab[tab_off_i + ((Dk - hi + W_i) >> 1)];
+        else return pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, Dk));
+    };
     uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
     load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
-    decide_group<G>(a, i, t0, acc, oldw, neww);
+#pragma unroll
+    for (int w = 0; w < Pack<G>::W; ++w) neww[w] = 0;
+    if constexpr (G == 1) {
+        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
+        const bool odd = t0 & 1;
+        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr_of(D[0]), thr, sbyte(oldw[0], 0));
+        neww[0] = (uint32_t)(uint8_t)(int8_t)s;
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k += 2) {
+            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo,
+                                   a.seed_hi);
+            const int s0 = pbit_next(r.x, r.y, kthr_of(D[k]), thr, sbyte(oldw[k >> 2], k & 3));
+            const int s1 = pbit_next(r.z, r.w, kthr_of(D[k + 1]), thr, sbyte(oldw[k >> 2], (k & 3) + 1));
+            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
+            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
+        }
+    }
     store_group<G>(a.out + (size_t)i * a.T + t0, neww);
 }
 
-template <int G>
+template <int G, bool UNIT, bool TABLE>
 cudaError_t launch_step_g(const StepArgs& a, cudaStream_t s) {
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
-    sparse_step_kernel<G><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    sparse_step_kernel<G, UNIT, TABLE><<<(unsigned)blocks, kBlock, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t launch_step_variant(const StepArgs& a, cudaStream_t s, SparseVariant v) {
+    if constexpr (G >= 4) {
+        if (v.unit && v.table) return launch_step_g<G, true, true>(a, s);
+        if (v.unit) return launch_step_g<G, true, false>(a, s);
+    }
+    if (v.table) return launch_step_g<G, false, true>(a, s);
+    return launch_step_g<G, false, false>(a, s);
 }
 
 // -------------------------------------------------------------- resident ----
@@ -278,6 +385,12 @@ __global__ void finish_cut_energy(long long* v, int32_t T, bool energy) {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
+int group_size(const StepArgs& a) {
+    if (a.T % 16 == 0 && aligned16(a.in) && aligned16(a.out)) return 16;
+    if (a.T % 4 == 0 && aligned4(a.in) && aligned4(a.out)) return 4;
+    return 1;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers ----
@@ -293,10 +406,26 @@ cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t inst
     return cudaGetLastError();
 }
 
-cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s) {
-    if (a.T % 16 == 0 && aligned16(a.in) && aligned16(a.out)) return launch_step_g<16>(a, s);
-    if (a.T % 4 == 0 && aligned4(a.in) && aligned4(a.out)) return launch_step_g<4>(a, s);
-    return launch_step_g<1>(a, s);
+SparseVariant choose_sparse_variant(const Graph& g, int32_t T) {
+    SparseVariant v;
+    static const bool plain = std::getenv("PBIT_SPARSE_PLAIN") != nullptr;  // force the plain variant
+    if (plain) return v;
+    const int G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
+    v.unit = g.unit_weights && g.max_degree <= 127 && G >= 4;
+    // table when its entries stay within shared memory and cost well under one per update
+    const int64_t groups = T / G;
+    const int64_t nodes_per_block = (kBlock + groups - 1) / groups + 1;
+    const int64_t entries = nodes_per_block * ((int64_t)g.max_wabs + 1);
+    v.table = g.tab_ok && entries <= kTabMax && entries * 4 <= (int64_t)kBlock * G * 3;
+    return v;
+}
+
+cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v) {
+    if (v.table && (!a.wabs || !a.tab_off)) v.table = false;
+    const int G = group_size(a);
+    if (G == 16) return launch_step_variant<16>(a, s, v);
+    if (G == 4) return launch_step_variant<4>(a, s, v);
+    return launch_step_variant<1>(a, s, v);
 }
 
 bool resident_fits(const Graph& g, int32_t T) {

@@ -212,3 +212,52 @@ def test_mismatch_rate_below_bound():
     assert dec >= 1.5e7
     assert mis == 0 or worst < BAND
     assert mis < 1e-6 * dec
+
+
+@pytest.mark.parametrize("T", [64, 256, 48])
+def test_table_variant_with_weights_and_bias(T):
+    """Small-range fields (|w| <= 3, h != 0): the shared-memory threshold table path vs the oracle."""
+    g = inputs.erdos_renyi_gnm(1500, 4500, 6, "+1")
+    g.w = np.random.default_rng(6).integers(-3, 4, g.m).astype(np.int8)
+    h = np.random.default_rng(7).integers(-4, 5, g.n).astype(np.int32)
+    var = inputs.variability(g.n, 6, s_intensity=0.3, s_offset=0.3)
+    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    S = 30
+    tab = oracle.schedule(csr, 0.1, 10.0, S)
+    state = inputs.random_spins(g.n, T, 2)
+    for t in range(0, S, 4):
+        d_in = _dev(state)
+        d_out = torch.empty_like(d_in)
+        p, keep = pbit.make_params(T, S, step_begin=t, step_end=t + 1, seed=3, variability=var,
+                                   kernel=pbit.KERNEL_SPARSE)
+        pbit.pbit_anneal(G.handle, p, d_in, d_out)
+        gpu = _host(d_out)
+        want, gap = oracle.step(csr, state, t, tab[t], 3, variability=var, h=h, want_gap=True)
+        bad = gpu != want
+        assert not bad.any() or np.abs(gap[bad]).max() < BAND
+        state = gpu
+
+
+def test_kernel_variants_agree(tmp_path):
+    """Packed-count and table variants give exactly the plain variant's spins (plain forced in a child)."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2601_14476_gb300 import inputs, pbit\n"
+        "outs = []\n"
+        "for g, T in ((inputs.torus_2d(40, 60, 3, 'pm1'), 256), (inputs.erdos_renyi_gnm(900, 2700, 4, '+1'), 64),\n"
+        "             (inputs.rgg_knn(1200, 5, 3, 'pm1'), 32), (inputs.erdos_renyi_gnm(800, 19176, 1, '+1'), 16)):\n"
+        "    G = pbit.Graph.from_inputs(g)\n"
+        "    var = inputs.variability(g.n, 2)\n"
+        "    outs.append(G.anneal(T, 40, seed=9, variability=var, kernel=pbit.KERNEL_SPARSE).cpu().numpy())\n"
+        "np.savez(%r, *outs)\n")
+    res = []
+    for k, extra in enumerate(({}, {"PBIT_SPARSE_PLAIN": "1"})):
+        path = str(tmp_path / f"v{k}.npz")
+        subprocess.run([sys.executable, "-c", code % path], check=True, env=dict(os.environ, **extra), timeout=300)
+        res.append(np.load(path))
+    for key in res[0].files:
+        assert np.array_equal(res[0][key], res[1][key]), key
