@@ -249,6 +249,62 @@ pbit_status pbit_cut(pbit_graph g, const int8_t* spins, int32_t trials, int64_t*
 pbit_status pbit_energy(pbit_graph g, const int8_t* spins, int32_t trials, int64_t* out, int32_t out_on_host,
                         void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched annealing: many instances of uneven size in one persistent        */
+/* launch per chunk of steps, replayed from a captured CUDA graph            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct pbit_batch_s* pbit_batch;
+
+/*
+ * Build a batch of `count` anneals.  graphs[k] must stay alive until the
+ * batch is destroyed; params[k] gives trials, schedule, range, seed,
+ * instance, offset mode and HOST variability arrays (copied; `kernel` and
+ * `stream` are ignored).  Device memory: two int8 spin buffers of n*T per
+ * instance plus its tables.  Each instance starts from the Philox initial
+ * state of its (seed, instance) (pbit_batch_set_spins replaces it).
+ * Synchronous.  Results equal pbit_anneal's for the same parameters.
+ */
+pbit_status pbit_batch_create(int32_t count, const pbit_graph* graphs, const pbit_anneal_params* params,
+                              pbit_batch* out);
+void pbit_batch_destroy(pbit_batch b);
+
+/* Copy DEVICE int8[n*T] spins into instance k's current state (stream-ordered). */
+pbit_status pbit_batch_set_spins(pbit_batch b, int32_t k, const int8_t* spins, void* stream);
+
+/*
+ * Advance every instance towards its step_end in chunks of `chunk_steps`
+ * schedule steps (0 keeps the current tuning), at most `max_chunks` chunks
+ * (0 = until every instance is done).  One chunk = one persistent kernel
+ * over all instances plus a small bookkeeping kernel, replayed from a CUDA
+ * graph.  Stream-ordered; does not wait for the GPU.
+ */
+pbit_status pbit_batch_run(pbit_batch b, int32_t chunk_steps, int32_t max_chunks, void* stream);
+
+/* Next schedule step of instance k, as enqueued so far. */
+pbit_status pbit_batch_progress(pbit_batch b, int32_t k, int32_t* step);
+
+/* Copy instance k's current spins to DEVICE int8[n*T] (stream-ordered). */
+pbit_status pbit_batch_spins(pbit_batch b, int32_t k, int8_t* spins_out, void* stream);
+
+/* Per-trial cut of instance k's current state into HOST int64[T]; synchronises `stream`. */
+pbit_status pbit_batch_cuts(pbit_batch b, int32_t k, int64_t* cuts, void* stream);
+
+typedef struct {
+    int32_t chunk_steps;   /* schedule steps per persistent launch */
+    int32_t ctas_per_sm;   /* persistent CTAs per SM (0 = occupancy maximum) */
+    float ms_per_step;     /* measured time of one step of the whole batch */
+} pbit_batch_tuning;
+
+/*
+ * Autotuner: times one chunk for each (chunk_steps in {8,16,32,64},
+ * ctas_per_sm in {1,2,4,max}) from the current state, restoring the state
+ * after every trial, and keeps the fastest.  Tiling never changes results.
+ * Synchronises `stream`.
+ */
+pbit_status pbit_batch_autotune(pbit_batch b, void* stream, pbit_batch_tuning* chosen);
+pbit_status pbit_batch_set_tuning(pbit_batch b, int32_t chunk_steps, int32_t ctas_per_sm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,96 +12,12 @@
 
 #include "pbit_device.cuh"
 #include "pbit_internal.h"
+#include "pbit_tile.cuh"
 
 namespace pbit {
 namespace {
 
-constexpr int kBlock = 256;
-
-template <int G>
-struct Pack {
-    static constexpr int W = (G + 3) / 4;  // 32-bit words per group
-};
-
-template <int G>
-__device__ __forceinline__ void load_group(const int8_t* p, uint32_t (&w)[Pack<G>::W]) {
-    if constexpr (G == 16) {
-        const int4 v = *reinterpret_cast<const int4*>(p);
-        w[0] = (uint32_t)v.x;
-        w[1] = (uint32_t)v.y;
-        w[2] = (uint32_t)v.z;
-        w[3] = (uint32_t)v.w;
-    } else if constexpr (G == 4) {
-        w[0] = *reinterpret_cast<const uint32_t*>(p);
-    } else {
-        w[0] = (uint32_t)(uint8_t)(*p);
-    }
-}
-
-template <int G>
-__device__ __forceinline__ void store_group(int8_t* p, const uint32_t (&w)[Pack<G>::W]) {
-    if constexpr (G == 16) {
-        *reinterpret_cast<int4*>(p) = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
-    } else if constexpr (G == 4) {
-        *reinterpret_cast<uint32_t*>(p) = w[0];
-    } else {
-        *p = (int8_t)(w[0] & 0xFF);
-    }
-}
-
-__device__ __forceinline__ int sbyte(uint32_t w, int k) { return (int)(int8_t)(uint8_t)(w >> (8 * k)); }
-
-// Exact field of node i for trials t0..t0+G-1 read from `in` (global or shared).
-template <int G>
-__device__ __forceinline__ void gather_field(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                             const int8_t* __restrict__ J, const int8_t* in, int32_t T, int i,
-                                             int t0, int (&acc)[G]) {
-#pragma unroll
-    for (int k = 0; k < G; ++k) acc[k] = 0;
-    const int rb = __ldg(row_ptr + i), re = __ldg(row_ptr + i + 1);
-    for (int e = rb; e < re; ++e) {
-        const int j = __ldg(col + e);
-        const int w = __ldg(J + e);
-        uint32_t v[Pack<G>::W];
-        load_group<G>(in + (size_t)j * T + t0, v);
-#pragma unroll
-        for (int k = 0; k < G; ++k) acc[k] += w * sbyte(v[k >> 2], k & 3);
-    }
-}
-
-// Decisions for one group of G trials of node i at `step` (Eq. 6 p-bit with
-// timing draw), from exact fields acc (without h) and old state words.
-template <int G>
-__device__ __forceinline__ void decide_group(const StepArgs& a, int i, int t0, const int (&acc)[G],
-                                             const uint32_t (&oldw)[Pack<G>::W], uint32_t (&neww)[Pack<G>::W]) {
-    const float I0 = __ldg(a.i0_table + a.step);
-    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
-    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
-    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
-    const int hi = a.h ? __ldg(a.h + i) : 0;
-#pragma unroll
-    for (int k = 0; k < Pack<G>::W; ++k) neww[k] = 0;
-    if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
-        const bool odd = t0 & 1;
-        const uint32_t wr = odd ? r.z : r.x, wu = odd ? r.w : r.y;
-        const uint32_t kthr = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[0]));
-        const int s = pbit_next(wr, wu, kthr, thr, sbyte(oldw[0], 0));
-        neww[0] = (uint32_t)(uint8_t)(int8_t)s;
-    } else {
-#pragma unroll
-        for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo,
-                                   a.seed_hi);
-            const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k]));
-            const uint32_t k1 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k + 1]));
-            const int s0 = pbit_next(r.x, r.y, k0, thr, sbyte(oldw[k >> 2], k & 3));
-            const int s1 = pbit_next(r.z, r.w, k1, thr, sbyte(oldw[k >> 2], (k & 3) + 1));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
-        }
-    }
-}
+using namespace tile;
 
 // ------------------------------------------------------------------ init ----
 __global__ void init_spins_kernel(int32_t n, int32_t T, uint32_t k0, uint32_t k1, uint32_t instance,
@@ -117,115 +33,10 @@ __global__ void init_spins_kernel(int32_t n, int32_t T, uint32_t k0, uint32_t k1
 }
 
 // ------------------------------------------------------------------ step ----
-// One thread per (node i, group of G trials); 256-thread blocks cover a
-// contiguous range of nodes.
-//
-// UNIT (every |J| = 1, degree <= 127): the gather counts, per trial byte,
-// the neighbours whose product J_ij * s_j is -1.  A spin byte is 0x01 (+1)
-// or 0xFF (-1), so (byte & 2) is 2 exactly for -1; XOR with 2 when J = -1
-// flips it.  Byte lanes of one 32-bit word add without carries (2 * 127 <
-// 256), and sum_j J_ij s_j = deg - 2 * count.
-//
-// TABLE: the field of node i lies in h_i + [-W_i, W_i] with the parity of
-// W_i (W_i = sum_j |J_ij|), so for this step the block first evaluates the
-// decision threshold for each of the W_i + 1 possible fields of its nodes
-// into shared memory; each update then reads its threshold by index
-// (D - h_i + W_i) / 2.  The table entries are computed by the same function
-// as the direct path, so both give identical decisions.
-constexpr int kTabMax = 4096;  // threshold entries per block (16 KB)
-
 template <int G, bool UNIT, bool TABLE>
 __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
-    const int groups = a.T / G;
-    const int64_t total = (int64_t)a.n * groups;
-    const int64_t first = blockIdx.x * (int64_t)kBlock;
-    const int64_t tid = first + threadIdx.x;
-    const float I0 = __ldg(a.i0_table + a.step);
     __shared__ uint32_t s_tab[TABLE ? kTabMax : 1];
-    int tab_base = 0, i_first = 0;
-    if constexpr (TABLE) {
-        i_first = (int)(first / groups);
-        const int i_last = (int)(min(total - 1, first + kBlock - 1) / groups);
-        tab_base = __ldg(a.tab_off + i_first);
-        const int cnt = __ldg(a.tab_off + i_last + 1) - tab_base;
-        for (int e = threadIdx.x; e < cnt; e += kBlock) {
-            // node of entry e: the last i in [i_first, i_last] with tab_off[i] - base <= e
-            int lo = i_first, hi = i_last;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(a.tab_off + mid) - tab_base <= e) lo = mid; else hi = mid - 1;
-            }
-            const int node = lo;
-            const int idx = e - (__ldg(a.tab_off + node) - tab_base);
-            const int W = __ldg(a.wabs + node);
-            const int hi_n = a.h ? __ldg(a.h + node) : 0;
-            const float lam = a.par.lambda ? __ldg(a.par.lambda + node) : 1.0f;
-            const float del = a.par.delta ? __ldg(a.par.delta + node) : 0.0f;
-            s_tab[e] = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi_n - W + 2 * idx));
-        }
-        __syncthreads();
-    }
-    if (tid >= total) return;
-    const int i = (int)(tid / groups);
-    const int t0 = (int)(tid - (int64_t)i * groups) * G;
-    const int hi = a.h ? __ldg(a.h + i) : 0;
-    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
-    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
-    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
-    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
-
-    int D[G];  // exact fields, h included
-    if constexpr (UNIT && G >= 4) {
-        uint32_t cnt2[Pack<G>::W];
-#pragma unroll
-        for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] = 0;
-        for (int e = rb; e < re; ++e) {
-            const int j = __ldg(a.col + e);
-            const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
-            uint32_t v[Pack<G>::W];
-            load_group<G>(a.in + (size_t)j * a.T + t0, v);
-#pragma unroll
-            for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] += (v[w] & 0x02020202u) ^ flip;
-        }
-        const int deg = re - rb;
-#pragma unroll
-        for (int k = 0; k < G; ++k) D[k] = hi + deg - (int)((cnt2[k >> 2] >> (8 * (k & 3))) & 0xFFu);
-    } else {
-        int acc[G];
-        gather_field<G>(a.row_ptr, a.col, a.J, a.in, a.T, i, t0, acc);
-#pragma unroll
-        for (int k = 0; k < G; ++k) D[k] = hi + acc[k];
-    }
-    int tab_off_i = 0, W_i = 0;
-    if constexpr (TABLE) {
-        tab_off_i = __ldg(a.tab_off + i) - tab_base;
-        W_i = __ldg(a.wabs + i);
-    }
-    auto kthr_of = [&](int Dk) -> uint32_t {
-        if constexpr (TABLE) return s_tab[tab_off_i + ((Dk - hi + W_i) >> 1)];
-        else return pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, Dk));
-    };
-    uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
-    load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
-#pragma unroll
-    for (int w = 0; w < Pack<G>::W; ++w) neww[w] = 0;
-    if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
-        const bool odd = t0 & 1;
-        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr_of(D[0]), thr, sbyte(oldw[0], 0));
-        neww[0] = (uint32_t)(uint8_t)(int8_t)s;
-    } else {
-#pragma unroll
-        for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo,
-                                   a.seed_hi);
-            const int s0 = pbit_next(r.x, r.y, kthr_of(D[k]), thr, sbyte(oldw[k >> 2], k & 3));
-            const int s1 = pbit_next(r.z, r.w, kthr_of(D[k + 1]), thr, sbyte(oldw[k >> 2], (k & 3) + 1));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
-        }
-    }
-    store_group<G>(a.out + (size_t)i * a.T + t0, neww);
+    process_tile<G, UNIT, TABLE>(a, blockIdx.x * (int64_t)kBlock, s_tab);
 }
 
 template <int G, bool UNIT, bool TABLE>

@@ -56,6 +56,10 @@ class pbit_anneal_params(C.Structure):
                 ("stream", C.c_void_p)]
 
 
+class pbit_batch_tuning(C.Structure):
+    _fields_ = [("chunk_steps", C.c_int32), ("ctas_per_sm", C.c_int32), ("ms_per_step", C.c_float)]
+
+
 _LIB = None
 _LOCK = threading.Lock()
 _P = C.c_void_p
@@ -83,6 +87,15 @@ def _declare(lib):
         "pbit_graph_status": ([_P, _P], C.c_int),
         "pbit_cut": ([_P, _P, i32, _P, i32, _P], C.c_int),
         "pbit_energy": ([_P, _P, i32, _P, i32, _P], C.c_int),
+        "pbit_batch_create": ([i32, _P, _P, _P], C.c_int),
+        "pbit_batch_destroy": ([_P], None),
+        "pbit_batch_set_spins": ([_P, i32, _P, _P], C.c_int),
+        "pbit_batch_run": ([_P, i32, i32, _P], C.c_int),
+        "pbit_batch_progress": ([_P, i32, _P], C.c_int),
+        "pbit_batch_spins": ([_P, i32, _P, _P], C.c_int),
+        "pbit_batch_cuts": ([_P, i32, _P, _P], C.c_int),
+        "pbit_batch_autotune": ([_P, _P, _P], C.c_int),
+        "pbit_batch_set_tuning": ([_P, i32, i32], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -264,7 +277,100 @@ def pbit_cut_device(g, spins, trials, out, stream=None):
     _check(lib().pbit_cut(g, _dev(spins), int(trials), _dev(out), 0, _stream(stream)))
 
 
+def pbit_batch_create(graphs, params):
+    """graphs: list of handles; params: list of pbit_anneal_params (host arrays kept alive by the caller)."""
+    n = len(graphs)
+    garr = (C.c_void_p * n)(*[g.value if isinstance(g, C.c_void_p) else g for g in graphs])
+    parr = (pbit_anneal_params * n)(*params)
+    out = _P()
+    _check(lib().pbit_batch_create(n, garr, parr, C.byref(out)))
+    return out
+
+
+def pbit_batch_destroy(b):
+    if b:
+        lib().pbit_batch_destroy(b)
+
+
+def pbit_batch_set_spins(b, k, spins, stream=None):
+    _check(lib().pbit_batch_set_spins(b, int(k), _dev(spins), _stream(stream)))
+
+
+def pbit_batch_run(b, chunk_steps=0, max_chunks=0, stream=None):
+    _check(lib().pbit_batch_run(b, int(chunk_steps), int(max_chunks), _stream(stream)))
+
+
+def pbit_batch_progress(b, k) -> int:
+    out = C.c_int32()
+    _check(lib().pbit_batch_progress(b, int(k), C.byref(out)))
+    return out.value
+
+
+def pbit_batch_spins(b, k, out, stream=None):
+    _check(lib().pbit_batch_spins(b, int(k), _dev(out), _stream(stream)))
+
+
+def pbit_batch_cuts(b, k, trials, stream=None) -> np.ndarray:
+    out = np.zeros(int(trials), np.int64)
+    _check(lib().pbit_batch_cuts(b, int(k), out.ctypes.data_as(_P), _stream(stream)))
+    return out
+
+
+def pbit_batch_autotune(b, stream=None) -> dict:
+    t = pbit_batch_tuning()
+    _check(lib().pbit_batch_autotune(b, _stream(stream), C.byref(t)))
+    return {"chunk_steps": t.chunk_steps, "ctas_per_sm": t.ctas_per_sm, "ms_per_step": t.ms_per_step}
+
+
+def pbit_batch_set_tuning(b, chunk_steps, ctas_per_sm=0):
+    _check(lib().pbit_batch_set_tuning(b, int(chunk_steps), int(ctas_per_sm)))
+
+
 # ------------------------------------------------------------ convenience ---
+
+class Batch:
+    """Owning wrapper of a pbit_batch over Graph objects and per-instance keyword parameters."""
+
+    def __init__(self, graphs, kwargs_list):
+        self.graphs = list(graphs)
+        self._keep = []
+        params = []
+        for kw in kwargs_list:
+            p, keep = make_params(**kw)
+            params.append(p)
+            self._keep.append(keep)
+        self.trials = [int(kw["trials"]) for kw in kwargs_list]
+        self.handle = pbit_batch_create([g.handle for g in self.graphs], params)
+
+    def run(self, chunk_steps=0, max_chunks=0, stream=None):
+        pbit_batch_run(self.handle, chunk_steps, max_chunks, stream)
+
+    def autotune(self, stream=None):
+        return pbit_batch_autotune(self.handle, stream)
+
+    def spins(self, k, stream=None):
+        import torch
+        out = torch.empty((self.graphs[k].n, self.trials[k]), dtype=torch.int8, device="cuda")
+        pbit_batch_spins(self.handle, k, out, stream)
+        return out
+
+    def cuts(self, k, stream=None):
+        return pbit_batch_cuts(self.handle, k, self.trials[k], stream)
+
+    def progress(self, k):
+        return pbit_batch_progress(self.handle, k)
+
+    def close(self):
+        if self.handle:
+            pbit_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
 
 class Graph:
     """Owning wrapper of a pbit_graph handle."""
