@@ -305,6 +305,57 @@ typedef struct {
 pbit_status pbit_batch_autotune(pbit_batch b, void* stream, pbit_batch_tuning* chosen);
 pbit_status pbit_batch_set_tuning(pbit_batch b, int32_t chunk_steps, int32_t ctas_per_sm);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of MAX-CUT solve requests                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct pbit_server_s* pbit_server;
+
+/*
+ * Start a server on the current device: a worker thread with its own stream
+ * that keeps up to `max_slots` requests resident, admits queued requests in
+ * arrival order while their device memory fits `hbm_budget` bytes, and
+ * advances every resident request by up to `chunk_steps` schedule steps per
+ * persistent launch.  Finished requests are retired (exact cuts computed)
+ * and their memory freed between launches.
+ */
+pbit_status pbit_server_create(size_t hbm_budget, int32_t max_slots, int32_t chunk_steps, pbit_server* out);
+
+/* Stop the worker after the resident requests finish; queued ones are cancelled. */
+void pbit_server_destroy(pbit_server s);
+
+/*
+ * Queue one anneal (the same parameters as pbit_anneal; host variability
+ * arrays are copied).  `g` must stay alive until the request's result has
+ * been taken.  PBIT_E_BUDGET if the request alone needs more device memory
+ * than the budget (2*n*T spin bytes + 4*steps + 12*n + 1 KiB).
+ */
+pbit_status pbit_server_submit(pbit_server s, pbit_graph g, const pbit_anneal_params* p, uint64_t* req_id);
+
+/*
+ * PBIT_PENDING while the request is queued or running; PBIT_OK once done,
+ * filling HOST int64[T] `cuts` and the seconds from submission to completion
+ * in `latency_s` (either may be NULL) and forgetting the request;
+ * PBIT_E_NOTFOUND for an unknown or already-taken id.
+ */
+pbit_status pbit_server_poll(pbit_server s, uint64_t req_id, int64_t* cuts, double* latency_s);
+
+/* As pbit_server_poll, but blocks up to timeout_s seconds (<= 0: no limit). */
+pbit_status pbit_server_wait(pbit_server s, uint64_t req_id, double timeout_s, int64_t* cuts, double* latency_s);
+
+typedef struct {
+    uint64_t completed;     /* requests finished */
+    uint64_t queued;        /* waiting for admission */
+    int32_t resident;       /* currently on the device */
+    int32_t peak_resident;  /* most requests resident in one launch */
+    uint64_t chunks;        /* persistent launches so far */
+    double spin_updates;    /* total spin updates executed */
+    double busy_seconds;    /* wall time spent inside launches */
+    size_t hbm_in_use;      /* device bytes held by resident requests */
+} pbit_server_stats_t;
+
+pbit_status pbit_server_stats(pbit_server s, pbit_server_stats_t* out);
+
 #ifdef __cplusplus
 }
 #endif

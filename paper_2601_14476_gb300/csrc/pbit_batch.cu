@@ -190,6 +190,99 @@ struct pbit_batch_s {
 
 namespace {
 
+// Device state of one instance: schedule table, per-node parameters, two
+// spin buffers (initial state from Philox).  Allocations are appended to
+// `allocs`; `host_keep` (optional) receives host arrays that must outlive the
+// asynchronous copies.  Stream-ordered on `s`.
+pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_t s, std::vector<void*>& allocs,
+                       InstDesc& d, std::vector<std::vector<uint32_t>>* host_keep) {
+    const pbit_anneal_params* p = &pp;
+    if (p->struct_size != sizeof(pbit_anneal_params)) return fail(PBIT_E_INVALID, "instance: struct_size mismatch");
+    const int32_t T = p->trials, S = p->steps;
+    const int32_t sb = p->step_begin, se = p->step_end == 0 ? S : p->step_end;
+    if (T < 1 || S < 1 || sb < 0 || se < sb || se > S || p->offset_mode < 0 || p->offset_mode > 2)
+        return fail(PBIT_E_INVALID, "instance: bad trials/steps/offset mode");
+    pbit_status st;
+    std::vector<float> tab;
+    if ((st = build_schedule(g, p->i0_min, p->i0_max, p->i0_normalize, S, tab)) != PBIT_OK) return st;
+    auto alloc = [&](void** ptr, size_t bytes) -> pbit_status {
+        cudaError_t e = cudaMallocAsync(ptr, bytes == 0 ? 16 : bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "instance: cudaMallocAsync");
+        allocs.push_back(*ptr);
+        return PBIT_OK;
+    };
+    std::memset(&d, 0, sizeof(d));
+    StepArgs& a = d.a;
+    a.row_ptr = g.row_ptr;
+    a.col = g.col;
+    a.J = g.J;
+    a.h = g.h;
+    a.wabs = g.wabs;
+    a.tab_off = g.tab_off;
+    a.n = g.n;
+    a.T = T;
+    a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
+    a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.instance = p->instance;
+    a.offset_mode = p->offset_mode;
+    const size_t n = (size_t)g.n;
+    // one block for the schedule and the parameters, copied from pageable memory (staged by CUDA)
+    void* d_tab = nullptr;
+    if ((st = alloc(&d_tab, sizeof(float) * tab.size())) != PBIT_OK) return st;
+    PBIT_CUDA_TRY(cudaMemcpyAsync(d_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s));
+    a.i0_table = (const float*)d_tab;
+    if (p->intensity) {
+        void* dp = nullptr;
+        if ((st = alloc(&dp, sizeof(float) * n)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemcpyAsync(dp, p->intensity, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        a.par.lambda = (const float*)dp;
+    }
+    if (p->offset) {
+        void* dp = nullptr;
+        if ((st = alloc(&dp, sizeof(float) * n)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemcpyAsync(dp, p->offset, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        a.par.delta = (const float*)dp;
+    }
+    if (p->p_update) {
+        std::vector<uint32_t> thr(n);
+        for (size_t i = 0; i < n; ++i) {
+            const float pu = p->p_update[i];
+            if (!(pu >= 0.0f && pu <= 1.0f)) return fail(PBIT_E_INVALID, "instance: p_update outside [0,1]");
+            thr[i] = (uint32_t)std::ceil((double)pu * 16777216.0);
+        }
+        void* dp = nullptr;
+        if ((st = alloc(&dp, sizeof(uint32_t) * n)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemcpyAsync(dp, thr.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+        a.par.thr = (const uint32_t*)dp;
+        if (host_keep) host_keep->push_back(std::move(thr));
+    }
+    const size_t cells = (n * (size_t)T + 15) / 16 * 16;
+    void* b0 = nullptr;
+    void* b1 = nullptr;
+    if ((st = alloc(&b0, cells)) != PBIT_OK) return st;
+    if ((st = alloc(&b1, cells)) != PBIT_OK) return st;
+    d.buf[0] = (int8_t*)b0;
+    d.buf[1] = (int8_t*)b1;
+    PBIT_CUDA_TRY(launch_init_spins(g.n, T, p->seed, p->instance, d.buf[0], s));
+    d.cur = sb;
+    d.end = se;
+    d.parity = 0;
+    d.G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
+    const SparseVariant v = choose_sparse_variant(g, T);
+    d.unit = v.unit ? 1 : 0;
+    d.table = v.table ? 1 : 0;
+    const int64_t items = (int64_t)g.n * (T / d.G);
+    d.tiles = (int32_t)((items + kBlock - 1) / kBlock);
+    d.active = 1;
+    return PBIT_OK;
+}
+
+// Bytes of device memory one instance needs (spins, schedule, parameters).
+size_t inst_bytes(const Graph& g, const pbit_anneal_params& p) {
+    const size_t n = (size_t)g.n;
+    return 2 * ((n * (size_t)p.trials + 15) / 16 * 16) + sizeof(float) * (size_t)p.steps + 12 * n + 1024;
+}
+
 template <typename T>
 pbit_status dev_alloc(pbit_batch b, T** p, size_t count) {
     if (count == 0) count = 1;
@@ -288,74 +381,10 @@ pbit_status pbit_batch_create(int32_t count, const pbit_graph* graphs, const pbi
     pbit_status st;
     for (int32_t k = 0; k < count; ++k) {
         const pbit_graph g = graphs[k];
-        const pbit_anneal_params* p = &params[k];
-        if (!g || p->struct_size != sizeof(pbit_anneal_params))
-            return fail(PBIT_E_INVALID, "batch_create: bad graph or params at " + std::to_string(k));
-        if (g->device != b->device) return fail(PBIT_E_INVALID, "batch_create: graphs on different devices");
-        const int32_t T = p->trials, S = p->steps;
-        const int32_t sb = p->step_begin, se = p->step_end == 0 ? S : p->step_end;
-        if (T < 1 || S < 1 || sb < 0 || se < sb || se > S || p->offset_mode < 0 || p->offset_mode > 2)
-            return fail(PBIT_E_INVALID, "batch_create: bad trials/steps at " + std::to_string(k));
-        std::vector<float> tab;
-        if ((st = build_schedule(*g, p->i0_min, p->i0_max, p->i0_normalize, S, tab)) != PBIT_OK) return st;
+        if (!g || g->device != b->device)
+            return fail(PBIT_E_INVALID, "batch_create: bad graph or graphs on different devices at " + std::to_string(k));
         InstDesc& d = b->host_desc[(size_t)k];
-        std::memset(&d, 0, sizeof(d));
-        StepArgs& a = d.a;
-        a.row_ptr = g->row_ptr;
-        a.col = g->col;
-        a.J = g->J;
-        a.h = g->h;
-        a.wabs = g->wabs;
-        a.tab_off = g->tab_off;
-        a.n = g->n;
-        a.T = T;
-        a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
-        a.seed_hi = (uint32_t)(p->seed >> 32);
-        a.instance = p->instance;
-        a.offset_mode = p->offset_mode;
-        float* d_tab = nullptr;
-        if ((st = dev_alloc(b.get(), &d_tab, tab.size())) != PBIT_OK) return st;
-        PBIT_CUDA_TRY(cudaMemcpy(d_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
-        a.i0_table = d_tab;
-        const size_t n = (size_t)g->n;
-        if (p->intensity) {
-            float* dp = nullptr;
-            if ((st = dev_alloc(b.get(), &dp, n)) != PBIT_OK) return st;
-            PBIT_CUDA_TRY(cudaMemcpy(dp, p->intensity, sizeof(float) * n, cudaMemcpyHostToDevice));
-            a.par.lambda = dp;
-        }
-        if (p->offset) {
-            float* dp = nullptr;
-            if ((st = dev_alloc(b.get(), &dp, n)) != PBIT_OK) return st;
-            PBIT_CUDA_TRY(cudaMemcpy(dp, p->offset, sizeof(float) * n, cudaMemcpyHostToDevice));
-            a.par.delta = dp;
-        }
-        if (p->p_update) {
-            std::vector<uint32_t> thr(n);
-            for (size_t i = 0; i < n; ++i) {
-                const float pu = p->p_update[i];
-                if (!(pu >= 0.0f && pu <= 1.0f)) return fail(PBIT_E_INVALID, "batch_create: p_update outside [0,1]");
-                thr[i] = (uint32_t)std::ceil((double)pu * 16777216.0);
-            }
-            uint32_t* dp = nullptr;
-            if ((st = dev_alloc(b.get(), &dp, n)) != PBIT_OK) return st;
-            PBIT_CUDA_TRY(cudaMemcpy(dp, thr.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
-            a.par.thr = dp;
-        }
-        const size_t cells = n * (size_t)T;
-        if ((st = dev_alloc(b.get(), &d.buf[0], (cells + 15) / 16 * 16)) != PBIT_OK) return st;
-        if ((st = dev_alloc(b.get(), &d.buf[1], (cells + 15) / 16 * 16)) != PBIT_OK) return st;
-        PBIT_CUDA_TRY(launch_init_spins(g->n, T, p->seed, p->instance, d.buf[0], s));
-        d.cur = sb;
-        d.end = se;
-        d.parity = 0;
-        d.G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
-        const SparseVariant v = choose_sparse_variant(*g, T);
-        d.unit = v.unit ? 1 : 0;
-        d.table = v.table ? 1 : 0;
-        const int64_t items = (int64_t)g->n * (T / d.G);
-        d.tiles = (int32_t)((items + kBlock - 1) / kBlock);
-        d.active = 1;
+        if ((st = build_inst(*g, params[k], s, b->allocs, d, nullptr)) != PBIT_OK) return st;
         b->tile_prefix[(size_t)k + 1] = b->tile_prefix[(size_t)k] + d.tiles;
     }
     b->total_tiles = b->tile_prefix[(size_t)count];
@@ -492,6 +521,314 @@ pbit_status pbit_batch_set_tuning(pbit_batch b, int32_t chunk_steps, int32_t cta
     if (!b || chunk_steps < 1 || ctas_per_sm < 0) return fail(PBIT_E_INVALID, "batch_set_tuning: bad argument");
     b->chunk = chunk_steps;
     b->ctas_per_sm = ctas_per_sm;
+    return PBIT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- server ----
+// Continuous batching: a worker thread owns a stream and a slot table of
+// resident instances.  Between chunks it retires finished instances (exact
+// cuts, latency), frees their memory, and admits queued requests while the
+// HBM budget and the slot count allow; each chunk is one persistent launch
+// over every resident instance.  Requests that arrive while others run join
+// at the next chunk boundary, so their work overlaps on the device.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t id = 0;
+    pbit_graph g = nullptr;
+    pbit_anneal_params p{};
+    std::vector<float> lam, del, pu;
+    size_t bytes = 0;
+    Clock::time_point t_submit, t_done;
+    int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+    pbit_status err = PBIT_OK;
+    std::vector<int64_t> cuts;
+    InstDesc desc{};
+    std::vector<void*> allocs;
+    std::vector<std::vector<uint32_t>> keep;
+};
+
+}  // namespace
+
+struct pbit_server_s {
+    int device = 0;
+    size_t budget = 0, in_use = 0;
+    int32_t max_slots = 0, chunk = 64;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::vector<uint64_t> running;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+    cudaStream_t stream = nullptr;
+    InstDesc* d_inst = nullptr;
+    int32_t* d_prefix = nullptr;
+    unsigned* d_ctl = nullptr;
+    int* d_err = nullptr;
+    // statistics
+    uint64_t completed = 0, chunks = 0;
+    double updates = 0.0, busy_s = 0.0;
+    int32_t peak_resident = 0;
+};
+
+namespace {
+
+void server_loop(pbit_server_s* S) {
+    cudaSetDevice(S->device);
+    std::vector<InstDesc> desc;
+    std::vector<int32_t> prefix;
+    for (;;) {
+        std::vector<Request*> active;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // admission: FIFO while a slot and the budget allow
+            while (!S->queue.empty() && (int32_t)S->running.size() < S->max_slots) {
+                Request* r = S->reqs[S->queue.front()].get();
+                if (S->in_use + r->bytes > S->budget) break;
+                S->queue.pop_front();
+                S->in_use += r->bytes;
+                r->state = 1;
+                S->running.push_back(r->id);
+                lk.unlock();
+                pbit_status st = build_inst(*r->g, r->p, S->stream, r->allocs, r->desc, &r->keep);
+                lk.lock();
+                if (st != PBIT_OK) {
+                    r->state = 3;
+                    r->err = st;
+                    S->running.pop_back();
+                    S->in_use -= r->bytes;
+                    S->done_cv.notify_all();
+                }
+            }
+            if (S->running.empty()) {
+                if (S->stop) return;
+                S->cv.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
+            }
+            for (uint64_t id : S->running) active.push_back(S->reqs[id].get());
+            S->peak_resident = std::max<int32_t>(S->peak_resident, (int32_t)active.size());
+        }
+        // one chunk over every resident instance
+        const auto t0 = Clock::now();
+        const int32_t count = (int32_t)active.size();
+        desc.resize((size_t)count);
+        prefix.assign((size_t)count + 1, 0);
+        double upd = 0.0;
+        for (int32_t k = 0; k < count; ++k) {
+            desc[(size_t)k] = active[(size_t)k]->desc;
+            prefix[(size_t)k + 1] = prefix[(size_t)k] + desc[(size_t)k].tiles;
+            const InstDesc& d = desc[(size_t)k];
+            upd += (double)d.a.n * d.a.T * std::min(S->chunk, d.end - d.cur);
+        }
+        cudaMemcpyAsync(S->d_inst, desc.data(), sizeof(InstDesc) * (size_t)count, cudaMemcpyHostToDevice, S->stream);
+        cudaMemcpyAsync(S->d_prefix, prefix.data(), sizeof(int32_t) * ((size_t)count + 1), cudaMemcpyHostToDevice,
+                        S->stream);
+        cudaMemsetAsync(S->d_ctl, 0, sizeof(unsigned) * ((size_t)count + 1), S->stream);
+        ChunkArgs c{};
+        c.inst = S->d_inst;
+        c.tile_prefix = S->d_prefix;
+        c.count = count;
+        c.total_tiles = prefix[(size_t)count];
+        c.K = S->chunk;
+        c.queue = S->d_ctl;
+        c.tiles_done = S->d_ctl + 1;
+        c.err = S->d_err;
+        int sms = 0, occ = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel, kBlock, 0);
+        batch_chunk_kernel<<<std::max(1, sms * std::max(1, occ)), kBlock, 0, S->stream>>>(c);
+        count_launches(1);
+        cudaError_t ce = cudaStreamSynchronize(S->stream);
+        const auto t1 = Clock::now();
+        // retire finished instances
+        std::vector<Request*> finished;
+        for (int32_t k = 0; k < count; ++k) {
+            Request* r = active[(size_t)k];
+            InstDesc& d = r->desc;
+            const int ran = std::min(S->chunk, std::max(0, d.end - d.cur));
+            d.cur += ran;
+            d.parity = (d.parity + ran) & 1;
+            if (d.cur >= d.end || ce != cudaSuccess) finished.push_back(r);
+        }
+        for (Request* r : finished) {
+            r->cuts.assign((size_t)r->p.trials, 0);
+            pbit_status st = ce == cudaSuccess ? pbit_cut(r->g, r->desc.buf[r->desc.parity], r->p.trials,
+                                                          r->cuts.data(), 1, S->stream)
+                                               : cuda_fail(ce, "server chunk");
+            for (void* p : r->allocs) cudaFreeAsync(p, S->stream);
+            r->allocs.clear();
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->t_done = Clock::now();
+            r->state = st == PBIT_OK ? 2 : 3;
+            r->err = st;
+            S->in_use -= r->bytes;
+            S->running.erase(std::find(S->running.begin(), S->running.end(), r->id));
+            S->completed += 1;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->chunks += 1;
+            S->updates += upd;
+            S->busy_s += std::chrono::duration<double>(t1 - t0).count();
+        }
+        if (!finished.empty()) S->done_cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+pbit_status pbit_server_create(size_t hbm_budget, int32_t max_slots, int32_t chunk_steps, pbit_server* out) {
+    if (!out || hbm_budget == 0 || max_slots < 1 || chunk_steps < 1)
+        return fail(PBIT_E_INVALID, "server_create: bad argument");
+    *out = nullptr;
+    std::unique_ptr<pbit_server_s> S(new (std::nothrow) pbit_server_s());
+    if (!S) return fail(PBIT_E_NOMEM, "server_create: host allocation");
+    PBIT_CUDA_TRY(cudaGetDevice(&S->device));
+    S->budget = hbm_budget;
+    S->max_slots = max_slots;
+    S->chunk = chunk_steps;
+    PBIT_CUDA_TRY(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
+    PBIT_CUDA_TRY(cudaMalloc((void**)&S->d_inst, sizeof(InstDesc) * (size_t)max_slots));
+    PBIT_CUDA_TRY(cudaMalloc((void**)&S->d_prefix, sizeof(int32_t) * ((size_t)max_slots + 1)));
+    PBIT_CUDA_TRY(cudaMalloc((void**)&S->d_ctl, sizeof(unsigned) * ((size_t)max_slots + 1)));
+    PBIT_CUDA_TRY(cudaMalloc((void**)&S->d_err, sizeof(int)));
+    PBIT_CUDA_TRY(cudaMemset(S->d_err, 0, sizeof(int)));
+    pbit_server_s* raw = S.get();
+    S->worker = std::thread(server_loop, raw);
+    *out = S.release();
+    return PBIT_OK;
+}
+
+void pbit_server_destroy(pbit_server S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        // queued requests that never started are dropped
+        for (uint64_t id : S->queue) {
+            S->reqs[id]->state = 3;
+            S->reqs[id]->err = PBIT_E_INVALID;
+        }
+        S->queue.clear();
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(S->device);
+    cudaStreamSynchronize(S->stream);
+    cudaStreamDestroy(S->stream);
+    cudaFree(S->d_inst);
+    cudaFree(S->d_prefix);
+    cudaFree(S->d_ctl);
+    cudaFree(S->d_err);
+    cudaSetDevice(cur);
+    delete S;
+}
+
+pbit_status pbit_server_submit(pbit_server S, pbit_graph g, const pbit_anneal_params* p, uint64_t* req_id) {
+    if (!S || !g || !p || !req_id) return fail(PBIT_E_INVALID, "server_submit: bad argument");
+    if (p->struct_size != sizeof(pbit_anneal_params)) return fail(PBIT_E_INVALID, "server_submit: struct_size");
+    if (g->device != S->device) return fail(PBIT_E_INVALID, "server_submit: graph on another device");
+    const int32_t S_ = p->steps, e = p->step_end == 0 ? p->steps : p->step_end;
+    if (p->trials < 1 || S_ < 1 || p->step_begin < 0 || e < p->step_begin || e > S_)
+        return fail(PBIT_E_INVALID, "server_submit: bad trials/steps");
+    std::unique_ptr<Request> r(new (std::nothrow) Request());
+    if (!r) return fail(PBIT_E_NOMEM, "server_submit: host allocation");
+    r->g = g;
+    r->p = *p;
+    const size_t n = (size_t)g->n;
+    if (p->intensity) {
+        r->lam.assign(p->intensity, p->intensity + n);
+        r->p.intensity = r->lam.data();
+    }
+    if (p->offset) {
+        r->del.assign(p->offset, p->offset + n);
+        r->p.offset = r->del.data();
+    }
+    if (p->p_update) {
+        r->pu.assign(p->p_update, p->p_update + n);
+        r->p.p_update = r->pu.data();
+    }
+    r->bytes = inst_bytes(*g, *p);
+    if (r->bytes > S->budget) return fail(PBIT_E_BUDGET, "server_submit: request needs " +
+                                                             std::to_string(r->bytes) + " bytes, budget is " +
+                                                             std::to_string(S->budget));
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) return fail(PBIT_E_INVALID, "server_submit: server is stopping");
+        r->id = S->next_id++;
+        *req_id = r->id;
+        S->queue.push_back(r->id);
+        S->reqs[r->id] = std::move(r);
+    }
+    S->cv.notify_all();
+    return PBIT_OK;
+}
+
+static pbit_status take_result(pbit_server S, std::map<uint64_t, std::unique_ptr<Request>>::iterator it,
+                               int64_t* cuts, double* latency_s) {
+    Request* r = it->second.get();
+    if (r->state == 3) {
+        const pbit_status e = r->err != PBIT_OK ? r->err : PBIT_E_INVALID;
+        S->reqs.erase(it);
+        return fail(e, "server: request failed or was cancelled");
+    }
+    if (cuts) std::memcpy(cuts, r->cuts.data(), sizeof(int64_t) * r->cuts.size());
+    if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    S->reqs.erase(it);
+    return PBIT_OK;
+}
+
+pbit_status pbit_server_poll(pbit_server S, uint64_t req_id, int64_t* cuts, double* latency_s) {
+    if (!S) return fail(PBIT_E_INVALID, "server_poll: NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return fail(PBIT_E_NOTFOUND, "server_poll: unknown request id");
+    if (it->second->state < 2) return PBIT_PENDING;
+    return take_result(S, it, cuts, latency_s);
+}
+
+pbit_status pbit_server_wait(pbit_server S, uint64_t req_id, double timeout_s, int64_t* cuts, double* latency_s) {
+    if (!S) return fail(PBIT_E_INVALID, "server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(
+                                             timeout_s > 0 ? timeout_s : 1e9));
+    for (;;) {
+        auto it = S->reqs.find(req_id);
+        if (it == S->reqs.end()) return fail(PBIT_E_NOTFOUND, "server_wait: unknown request id");
+        if (it->second->state >= 2) return take_result(S, it, cuts, latency_s);
+        if (S->done_cv.wait_until(lk, deadline) == std::cv_status::timeout) return PBIT_PENDING;
+    }
+}
+
+pbit_status pbit_server_stats(pbit_server S, pbit_server_stats_t* out) {
+    if (!S || !out) return fail(PBIT_E_INVALID, "server_stats: bad argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->completed = S->completed;
+    out->queued = (uint64_t)S->queue.size();
+    out->resident = (int32_t)S->running.size();
+    out->peak_resident = S->peak_resident;
+    out->chunks = S->chunks;
+    out->spin_updates = S->updates;
+    out->busy_seconds = S->busy_s;
+    out->hbm_in_use = S->in_use;
     return PBIT_OK;
 }
 

@@ -60,6 +60,12 @@ class pbit_batch_tuning(C.Structure):
     _fields_ = [("chunk_steps", C.c_int32), ("ctas_per_sm", C.c_int32), ("ms_per_step", C.c_float)]
 
 
+class pbit_server_stats_t(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("queued", C.c_uint64), ("resident", C.c_int32),
+                ("peak_resident", C.c_int32), ("chunks", C.c_uint64), ("spin_updates", C.c_double),
+                ("busy_seconds", C.c_double), ("hbm_in_use", C.c_size_t)]
+
+
 _LIB = None
 _LOCK = threading.Lock()
 _P = C.c_void_p
@@ -96,6 +102,12 @@ def _declare(lib):
         "pbit_batch_cuts": ([_P, i32, _P, _P], C.c_int),
         "pbit_batch_autotune": ([_P, _P, _P], C.c_int),
         "pbit_batch_set_tuning": ([_P, i32, i32], C.c_int),
+        "pbit_server_create": ([C.c_size_t, i32, i32, _P], C.c_int),
+        "pbit_server_destroy": ([_P], None),
+        "pbit_server_submit": ([_P, _P, _P, _P], C.c_int),
+        "pbit_server_poll": ([_P, u64, _P, _P], C.c_int),
+        "pbit_server_wait": ([_P, u64, f64, _P, _P], C.c_int),
+        "pbit_server_stats": ([_P, _P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -324,6 +336,48 @@ def pbit_batch_autotune(b, stream=None) -> dict:
 
 def pbit_batch_set_tuning(b, chunk_steps, ctas_per_sm=0):
     _check(lib().pbit_batch_set_tuning(b, int(chunk_steps), int(ctas_per_sm)))
+
+
+def pbit_server_create(hbm_budget, max_slots, chunk_steps):
+    out = _P()
+    _check(lib().pbit_server_create(int(hbm_budget), int(max_slots), int(chunk_steps), C.byref(out)))
+    return out
+
+
+def pbit_server_destroy(s):
+    if s:
+        lib().pbit_server_destroy(s)
+
+
+def pbit_server_submit(s, g, params) -> int:
+    rid = C.c_uint64()
+    _check(lib().pbit_server_submit(s, g, C.byref(params), C.byref(rid)))
+    return rid.value
+
+
+def pbit_server_poll(s, req_id, trials):
+    """(status, cuts or None, latency seconds or None)."""
+    cuts = np.zeros(int(trials), np.int64)
+    lat = C.c_double()
+    code = _check(lib().pbit_server_poll(s, int(req_id), cuts.ctypes.data_as(_P), C.byref(lat)))
+    if code == PBIT_PENDING:
+        return code, None, None
+    return code, cuts, lat.value
+
+
+def pbit_server_wait(s, req_id, trials, timeout_s=0.0):
+    cuts = np.zeros(int(trials), np.int64)
+    lat = C.c_double()
+    code = _check(lib().pbit_server_wait(s, int(req_id), float(timeout_s), cuts.ctypes.data_as(_P), C.byref(lat)))
+    if code == PBIT_PENDING:
+        return code, None, None
+    return code, cuts, lat.value
+
+
+def pbit_server_stats(s) -> dict:
+    st = pbit_server_stats_t()
+    _check(lib().pbit_server_stats(s, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
 
 
 # ------------------------------------------------------------ convenience ---

@@ -1,0 +1,89 @@
+"""Serving with continuous batching: each request's result equals the same
+anneal run alone; requests overlap on the device; the HBM budget gates
+admission; poll/wait semantics."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2601_14476_gb300 import inputs, pbit
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _requests(seed=1, k=6):
+    out = []
+    for r in range(k):
+        w = inputs.serving_request(r, seed, n_lo=500, n_hi=3000, t_lo=16, t_hi=96, s_lo=40, s_hi=160)
+        out.append(w)
+    return out
+
+
+def _alone_cuts(G, w):
+    out = G.anneal(w.trials, w.steps, seed=w.seed, instance=w.instance, variability=w.var,
+                   i0_min=w.c_min, i0_max=w.c_max, kernel=pbit.KERNEL_SPARSE)
+    return G.cut(out)
+
+
+def test_server_results_equal_alone():
+    ws = _requests()
+    Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+    srv = pbit.pbit_server_create(8 << 30, 16, 16)
+    try:
+        keep, ids = [], []
+        for G, w in zip(Gs, ws):
+            p, k = pbit.make_params(w.trials, w.steps, seed=w.seed, instance=w.instance, variability=w.var,
+                                    i0_min=w.c_min, i0_max=w.c_max)
+            keep.append((p, k))
+            ids.append(pbit.pbit_server_submit(srv, G.handle, p))
+        for rid, G, w in zip(ids, Gs, ws):
+            code, cuts, lat = pbit.pbit_server_wait(srv, rid, w.trials, timeout_s=120)
+            assert code == pbit.PBIT_OK and lat > 0
+            assert np.array_equal(cuts, _alone_cuts(G, w))
+        st = pbit.pbit_server_stats(srv)
+        assert st["completed"] == len(ws) and st["peak_resident"] >= 2 and st["hbm_in_use"] == 0
+        with pytest.raises(pbit.PbitError) as ei:
+            pbit.pbit_server_poll(srv, ids[0], ws[0].trials)
+        assert ei.value.code == pbit.PBIT_E_NOTFOUND
+    finally:
+        pbit.pbit_server_destroy(srv)
+
+
+def test_server_overlap_and_budget():
+    long_w = inputs.Workload("long", inputs.torus_2d(100, 100, 2), 512, 4000, 0.1, 10.0, None, 5, 0)
+    short_w = inputs.Workload("short", inputs.erdos_renyi_gnm(500, 1500, 3, "+1"), 32, 50, 0.1, 10.0, None, 6, 1)
+    GL, GS = pbit.Graph.from_inputs(long_w.graph), pbit.Graph.from_inputs(short_w.graph)
+    srv = pbit.pbit_server_create(1 << 30, 8, 32)
+    try:
+        pl, kl = pbit.make_params(long_w.trials, long_w.steps, seed=5)
+        ps, ks = pbit.make_params(short_w.trials, short_w.steps, seed=6, instance=1)
+        a = pbit.pbit_server_submit(srv, GL.handle, pl)
+        time.sleep(0.05)
+        b = pbit.pbit_server_submit(srv, GS.handle, ps)
+        code, cuts_b, lat_b = pbit.pbit_server_wait(srv, b, short_w.trials, timeout_s=120)
+        assert code == pbit.PBIT_OK
+        # the short request finished while the long one was still resident
+        assert pbit.pbit_server_poll(srv, a, long_w.trials)[0] == pbit.PBIT_PENDING
+        code, cuts_a, lat_a = pbit.pbit_server_wait(srv, a, long_w.trials, timeout_s=300)
+        assert code == pbit.PBIT_OK and lat_b < lat_a
+        assert np.array_equal(cuts_a, _alone_cuts(GL, long_w))
+        assert np.array_equal(cuts_b, _alone_cuts(GS, short_w))
+    finally:
+        pbit.pbit_server_destroy(srv)
+    # a budget that holds one request at a time still serves all, one after another
+    srv = pbit.pbit_server_create(3 * 500 * 32 + 4 * 50 + 12 * 500 + 1024 + 1000, 8, 16)
+    try:
+        ids = []
+        for r in range(3):
+            p, k = pbit.make_params(32, 50, seed=10 + r, instance=r)
+            ids.append((pbit.pbit_server_submit(srv, GS.handle, p), p, k))
+        for rid, p, k in ids:
+            assert pbit.pbit_server_wait(srv, rid, 32, timeout_s=60)[0] == pbit.PBIT_OK
+        assert pbit.pbit_server_stats(srv)["peak_resident"] == 1
+        p, k = pbit.make_params(256, 50, seed=1)
+        with pytest.raises(pbit.PbitError) as ei:
+            pbit.pbit_server_submit(srv, GL.handle, p)
+        assert ei.value.code == pbit.PBIT_E_BUDGET
+    finally:
+        pbit.pbit_server_destroy(srv)
