@@ -155,6 +155,208 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- batch and serve ----
+
+def _dist_setup():
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local, dist
+
+
+def _max_over_ranks(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_multi(args):
+    """config batch: 64 uneven instances, batched persistent form vs plain one-instance-per-launch form.
+    config serve: Poisson request stream through the continuous-batching server, p50/p99 latency."""
+    import torch
+    from paper_2601_14476_gb300 import pbit
+    rank, world, local, dist = _dist_setup()
+    pk = peaks()
+    stream = torch.cuda.current_stream()
+    if args.config == "batch":
+        ws = inputs.batch64(seed=1 + rank, steps=args.anneal_steps or 2000)
+        Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+        kws = [dict(trials=w.trials, steps=w.steps, seed=w.seed, instance=w.instance, variability=w.var,
+                    i0_min=w.c_min, i0_max=w.c_max) for w in ws]
+        upd_run = sum(w.graph.n * w.trials * w.steps for w in ws)
+        bytes_run = sum(w.graph.n * w.trials * w.steps * (2.0 * w.graph.m / w.graph.n + 2.0) for w in ws)
+        B0 = pbit.Batch(Gs, kws)
+        tuning = B0.autotune(stream)
+        B0.close()
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+        def batched_run():
+            B = pbit.Batch(Gs, kws)
+            pbit.pbit_batch_set_tuning(B.handle, tuning["chunk_steps"], tuning["ctas_per_sm"])
+            return B
+
+        for _ in range(args.warmup):
+            B = batched_run()
+            B.run(stream=stream)
+            torch.cuda.synchronize()
+            B.close()
+        if dist:
+            dist.barrier()
+        times = []
+        launches0 = pbit.pbit_launch_count()
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                B = batched_run()          # instance setup is outside the timed region
+                flush.zero_()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                B.run(stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+                batched_cuts = [B.cuts(k) for k in range(len(ws))]
+                B.close()
+        launches = pbit.pbit_launch_count() - launches0
+        ms = _max_over_ranks(dist, float(np.mean(times)))
+        value = world * upd_run / (ms * 1e-3)
+        # plain form: one instance after another, one launch per step (or one resident launch)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        outs = [torch.empty((w.graph.n, w.trials), dtype=torch.int8, device="cuda") for w in ws]
+        a.record(stream)
+        for G, w, o, kw in zip(Gs, ws, outs, kws):
+            p, keep = pbit.make_params(stream=stream, **kw)
+            pbit.pbit_anneal(G.handle, p, None, o)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = a.elapsed_time(b)
+        plain_cuts = [G.cut(o) for G, o in zip(Gs, outs)]
+        same = all(np.array_equal(x, y) for x, y in zip(batched_cuts, plain_cuts))
+        mean_b = float(np.mean([c.mean() for c in batched_cuts]))
+        mean_p = float(np.mean([c.mean() for c in plain_cuts]))
+        # e2e: graphs from host arrays, batch setup, run, cuts back to host
+        t0 = time.perf_counter()
+        G2 = [pbit.Graph.from_inputs(w.graph) for w in ws]
+        B2 = pbit.Batch(G2, kws)
+        pbit.pbit_batch_set_tuning(B2.handle, tuning["chunk_steps"], tuning["ctas_per_sm"])
+        B2.run(stream=stream)
+        host_cuts = [B2.cuts(k) for k in range(len(ws))]
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        B2.close()
+        h2d = sum(w.graph.m * 9 + (12 * w.graph.n if w.var else 0) + 4 * w.steps for w in ws)
+        d2h = sum(8 * w.trials for w in ws)
+        achieved = bytes_run / (ms * 1e-3) / 1e9
+        line = {
+            "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
+            "config": {"workload": f"batch64_uneven_S{ws[0].steps}", "instances": len(ws),
+                       "n_range": [min(w.graph.n for w in ws), max(w.graph.n for w in ws)],
+                       "trials": sorted(set(w.trials for w in ws)), "updates_per_step": upd_run,
+                       "tuning": tuning, "l2": "flushed between timed steps",
+                       "plain_value": world * upd_run / (plain_ms * 1e-3), "plain_ms": plain_ms,
+                       "batched_over_plain": plain_ms / ms, "cuts_identical_to_plain": bool(same),
+                       "mean_cut_batched": mean_b, "mean_cut_plain": mean_p},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "batch_chunk_kernel",
+                         "peak_source": pk["source"],
+                         "per_launch": "sum over instances of (deg+2) bytes x n*T updates per step"},
+            "cpu_baseline": None,
+            "e2e": {"value": world * upd_run / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(ws[0])
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- serve: Poisson sweep
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    # a pool of request graphs (n log-uniform in [800, 20000], G(n,3n) w=+1 or 3-NN RGG w=+-1) built
+    # before the sweep; every request draws its own trials, steps, variability and seed
+    pool = []
+    for r in range(48):
+        w = inputs.serving_request(r, seed=1 + rank)
+        pool.append((pbit.Graph.from_inputs(w.graph), w, inputs.variability(w.graph.n, r)))
+    sweep = []
+    total_upd, total_wall = 0.0, 0.0
+    launches0 = pbit.pbit_launch_count()
+    with ClockSampler(local) as clk:
+        for ri, rate in enumerate(rates):
+            arrivals = inputs.poisson_arrivals(rate, args.serve_seconds, seed=100 + ri + 1000 * rank)
+            srv = pbit.pbit_server_create(64 << 30, 64, 64)
+            pending = {}
+            t_start = time.perf_counter()
+            upd = 0.0
+            for k, t_arr in enumerate(arrivals):
+                now = time.perf_counter() - t_start
+                if t_arr > now:
+                    time.sleep(t_arr - now)
+                T, S, with_var = inputs.serving_draw(k, seed=7 + ri)
+                G, w, var = pool[k % len(pool)]
+                p, keep = pbit.make_params(T, S, seed=k + 1, instance=k, variability=var if with_var else None)
+                t_sub = time.perf_counter()
+                rid = pbit.pbit_server_submit(srv, G.handle, p)
+                pending[rid] = (T, w.graph.n * T * S, keep, t_sub)
+            # drain for up to 20 s; a request still unfinished then counts with its age so far as a
+            # lower bound of its latency (censored)
+            lat, censored = [], 0
+            deadline = time.perf_counter() + 20.0
+            for rid, (T, u, keep, t_sub) in list(pending.items()):
+                left = deadline - time.perf_counter()
+                code = pbit.PBIT_PENDING
+                if left > 0:
+                    code, cuts, l = pbit.pbit_server_wait(srv, rid, T, timeout_s=left)
+                if code == pbit.PBIT_OK:
+                    lat.append(l)
+                    upd += u
+                else:
+                    lat.append(time.perf_counter() - t_sub)
+                    censored += 1
+            wall = time.perf_counter() - t_start
+            st = pbit.pbit_server_stats(srv)
+            pbit.pbit_server_destroy(srv)
+            total_upd += upd
+            total_wall += wall
+            sweep.append({"rate": rate, "submitted": len(arrivals), "completed": len(arrivals) - censored,
+                          "censored": censored,
+                          "p50_s": float(np.percentile(lat, 50)) if lat else None,
+                          "p99_s": float(np.percentile(lat, 99)) if lat else None,
+                          "updates_per_s": upd / wall, "peak_resident": st["peak_resident"]})
+    launches = pbit.pbit_launch_count() - launches0
+    value = world * total_upd / total_wall
+    line = {
+        "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
+        "steps": len(rates), "warmup": args.warmup, "ms_per_step": 1e3 * total_wall / max(1, len(rates)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
+        "config": {"workload": "poisson_serving", "rates": rates, "window_s": args.serve_seconds,
+                   "request_pool": len(pool), "sweep": sweep, "budget_bytes": 64 << 30, "max_slots": 64,
+                   "latency": "submit to result; unfinished after a 20 s drain enter with their age (censored)",
+                   "chunk_steps": 64, "l2": "inputs larger than L2 in aggregate"},
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------ main ----
 
 def main():
@@ -162,7 +364,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain"])
+    ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain", "batch", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window per rate (serve config)")
+    ap.add_argument("--serve-rates", default="10,30,100,300,1000")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "sparse", "dense", "resident"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -172,6 +376,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.config in ("batch", "serve"):
+        return bench_multi(args)
     w = workload(args.config)
     if args.anneal_steps > 0:
         w.steps = args.anneal_steps

@@ -41,6 +41,7 @@ struct InstDesc {
     int32_t G, unit, table;
     int32_t tiles;     // tiles per step
     int32_t active;    // 0 = slot unused
+    int32_t T_real;    // trials the caller asked for; a.T is the padded row stride
 };
 
 struct ChunkArgs {
@@ -219,8 +220,12 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     a.h = g.h;
     a.wabs = g.wabs;
     a.tab_off = g.tab_off;
+    // Rows are padded to a multiple of 16 trials (4 below 64 trials) so every
+    // instance runs the vectorised tile code; the extra trials are computed
+    // like the others (their Philox counters are their own) and never reported.
+    const int32_t T_pad = T % 16 == 0 ? T : (T >= 64 ? (T + 15) / 16 * 16 : (T + 3) / 4 * 4);
     a.n = g.n;
-    a.T = T;
+    a.T = T_pad;
     a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
     a.seed_hi = (uint32_t)(p->seed >> 32);
     a.instance = p->instance;
@@ -256,31 +261,42 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
         a.par.thr = (const uint32_t*)dp;
         if (host_keep) host_keep->push_back(std::move(thr));
     }
-    const size_t cells = (n * (size_t)T + 15) / 16 * 16;
+    const size_t cells = n * (size_t)T_pad;
     void* b0 = nullptr;
     void* b1 = nullptr;
     if ((st = alloc(&b0, cells)) != PBIT_OK) return st;
     if ((st = alloc(&b1, cells)) != PBIT_OK) return st;
     d.buf[0] = (int8_t*)b0;
     d.buf[1] = (int8_t*)b1;
-    PBIT_CUDA_TRY(launch_init_spins(g.n, T, p->seed, p->instance, d.buf[0], s));
+    PBIT_CUDA_TRY(launch_init_spins(g.n, T_pad, p->seed, p->instance, d.buf[0], s));
     d.cur = sb;
     d.end = se;
     d.parity = 0;
-    d.G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
-    const SparseVariant v = choose_sparse_variant(g, T);
+    d.G = T_pad % 16 == 0 ? 16 : 4;
+    d.T_real = T;
+    const SparseVariant v = choose_sparse_variant(g, T_pad);
     d.unit = v.unit ? 1 : 0;
     d.table = v.table ? 1 : 0;
-    const int64_t items = (int64_t)g.n * (T / d.G);
+    const int64_t items = (int64_t)g.n * (T_pad / d.G);
     d.tiles = (int32_t)((items + kBlock - 1) / kBlock);
     d.active = 1;
+    return PBIT_OK;
+}
+
+// Exact cuts of the T_real reported trials of an instance (rows padded to a.T).
+pbit_status padded_cuts(pbit_graph g, const InstDesc& d, int64_t* cuts, cudaStream_t s) {
+    std::vector<int64_t> all((size_t)d.a.T);
+    pbit_status st = pbit_cut(g, d.buf[d.parity], d.a.T, all.data(), 1, s);
+    if (st != PBIT_OK) return st;
+    std::memcpy(cuts, all.data(), sizeof(int64_t) * (size_t)d.T_real);
     return PBIT_OK;
 }
 
 // Bytes of device memory one instance needs (spins, schedule, parameters).
 size_t inst_bytes(const Graph& g, const pbit_anneal_params& p) {
     const size_t n = (size_t)g.n;
-    return 2 * ((n * (size_t)p.trials + 15) / 16 * 16) + sizeof(float) * (size_t)p.steps + 12 * n + 1024;
+    const size_t T_pad = (size_t)(p.trials + 15) / 16 * 16;
+    return 2 * n * T_pad + sizeof(float) * (size_t)p.steps + 12 * n + 1024;
 }
 
 template <typename T>
@@ -405,8 +421,8 @@ void pbit_batch_destroy(pbit_batch b) { delete b; }
 pbit_status pbit_batch_set_spins(pbit_batch b, int32_t k, const int8_t* spins, void* stream) {
     if (!b || k < 0 || k >= b->count || !spins) return fail(PBIT_E_INVALID, "batch_set_spins: bad argument");
     InstDesc& d = b->host_desc[(size_t)k];
-    const size_t cells = (size_t)d.a.n * (size_t)d.a.T;
-    PBIT_CUDA_TRY(cudaMemcpyAsync(d.buf[d.parity], spins, cells, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    PBIT_CUDA_TRY(cudaMemcpy2DAsync(d.buf[d.parity], (size_t)d.a.T, spins, (size_t)d.T_real, (size_t)d.T_real,
+                                    (size_t)d.a.n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return PBIT_OK;
 }
 
@@ -438,15 +454,15 @@ pbit_status pbit_batch_progress(pbit_batch b, int32_t k, int32_t* step) {
 pbit_status pbit_batch_spins(pbit_batch b, int32_t k, int8_t* spins_out, void* stream) {
     if (!b || k < 0 || k >= b->count || !spins_out) return fail(PBIT_E_INVALID, "batch_spins: bad argument");
     const InstDesc& d = b->host_desc[(size_t)k];
-    const size_t cells = (size_t)d.a.n * (size_t)d.a.T;
-    PBIT_CUDA_TRY(cudaMemcpyAsync(spins_out, d.buf[d.parity], cells, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    PBIT_CUDA_TRY(cudaMemcpy2DAsync(spins_out, (size_t)d.T_real, d.buf[d.parity], (size_t)d.a.T, (size_t)d.T_real,
+                                    (size_t)d.a.n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return PBIT_OK;
 }
 
 pbit_status pbit_batch_cuts(pbit_batch b, int32_t k, int64_t* cuts, void* stream) {
     if (!b || k < 0 || k >= b->count || !cuts) return fail(PBIT_E_INVALID, "batch_cuts: bad argument");
     const InstDesc& d = b->host_desc[(size_t)k];
-    return pbit_cut(b->graphs[(size_t)k], d.buf[d.parity], d.a.T, cuts, 1, stream);
+    return padded_cuts(b->graphs[(size_t)k], d, cuts, (cudaStream_t)stream);
 }
 
 // Time one chunk for each candidate (chunk length, CTAs per SM) from the
@@ -590,29 +606,32 @@ void server_loop(pbit_server_s* S) {
     cudaSetDevice(S->device);
     std::vector<InstDesc> desc;
     std::vector<int32_t> prefix;
+    // FIFO admission while a slot and the budget allow (caller holds the lock)
+    auto admit = [S](std::unique_lock<std::mutex>& lk) {
+        while (!S->queue.empty() && (int32_t)S->running.size() < S->max_slots) {
+            Request* r = S->reqs[S->queue.front()].get();
+            if (S->in_use + r->bytes > S->budget) break;
+            S->queue.pop_front();
+            S->in_use += r->bytes;
+            r->state = 1;
+            S->running.push_back(r->id);
+            lk.unlock();
+            pbit_status st = build_inst(*r->g, r->p, S->stream, r->allocs, r->desc, &r->keep);
+            lk.lock();
+            if (st != PBIT_OK) {
+                r->state = 3;
+                r->err = st;
+                S->running.erase(std::find(S->running.begin(), S->running.end(), r->id));
+                S->in_use -= r->bytes;
+                S->done_cv.notify_all();
+            }
+        }
+    };
     for (;;) {
         std::vector<Request*> active;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // admission: FIFO while a slot and the budget allow
-            while (!S->queue.empty() && (int32_t)S->running.size() < S->max_slots) {
-                Request* r = S->reqs[S->queue.front()].get();
-                if (S->in_use + r->bytes > S->budget) break;
-                S->queue.pop_front();
-                S->in_use += r->bytes;
-                r->state = 1;
-                S->running.push_back(r->id);
-                lk.unlock();
-                pbit_status st = build_inst(*r->g, r->p, S->stream, r->allocs, r->desc, &r->keep);
-                lk.lock();
-                if (st != PBIT_OK) {
-                    r->state = 3;
-                    r->err = st;
-                    S->running.pop_back();
-                    S->in_use -= r->bytes;
-                    S->done_cv.notify_all();
-                }
-            }
+            admit(lk);
             if (S->running.empty()) {
                 if (S->stop) return;
                 S->cv.wait_for(lk, std::chrono::milliseconds(20));
@@ -651,6 +670,11 @@ void server_loop(pbit_server_s* S) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel, kBlock, 0);
         batch_chunk_kernel<<<std::max(1, sms * std::max(1, occ)), kBlock, 0, S->stream>>>(c);
         count_launches(1);
+        {
+            // requests arriving meanwhile are prepared now and join at the next chunk
+            std::unique_lock<std::mutex> lk(S->mu);
+            admit(lk);
+        }
         cudaError_t ce = cudaStreamSynchronize(S->stream);
         const auto t1 = Clock::now();
         // retire finished instances
@@ -665,8 +689,7 @@ void server_loop(pbit_server_s* S) {
         }
         for (Request* r : finished) {
             r->cuts.assign((size_t)r->p.trials, 0);
-            pbit_status st = ce == cudaSuccess ? pbit_cut(r->g, r->desc.buf[r->desc.parity], r->p.trials,
-                                                          r->cuts.data(), 1, S->stream)
+            pbit_status st = ce == cudaSuccess ? padded_cuts(r->g, r->desc, r->cuts.data(), S->stream)
                                                : cuda_fail(ce, "server chunk");
             for (void* p : r->allocs) cudaFreeAsync(p, S->stream);
             r->allocs.clear();

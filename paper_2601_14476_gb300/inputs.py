@@ -224,6 +224,15 @@ def serving_request(req_id: int, seed: int = 1, n_lo: int = 800, n_hi: int = 200
     return Workload(f"req{req_id}_{g.name}_T{T}_S{S}", g, T, S, 0.1, 10.0, var, seed, req_id)
 
 
+def serving_draw(req_id: int, seed: int = 1, t_lo: int = 16, t_hi: int = 256, s_lo: int = 1000,
+                 s_hi: int = 10000):
+    """Trials, steps and variability flag of one serving request (no graph)."""
+    rng = np.random.default_rng([0x7264, seed, req_id])
+    T = int(rng.integers(t_lo, t_hi + 1))
+    S = int(rng.integers(s_lo, s_hi + 1))
+    return T, S, bool(rng.integers(0, 2) == 1)
+
+
 def poisson_arrivals(rate: float, duration_s: float, seed: int = 1) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process with the given rate."""
     rng = np.random.default_rng([0x706F, seed])
