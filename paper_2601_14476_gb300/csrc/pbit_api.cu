@@ -466,9 +466,10 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         PBIT_CUDA_TRY(launch_to_tiled(*g, cur, T, t0, s));
         // persistent form when every cluster can be resident, else one launch per step
         unsigned* done = nullptr;
-        const int RB = g->dense.n_pad / 128, TB = T <= 128 ? 1 : T / 128;
-        if ((st = cb.alloc(&done, (size_t)RB * TB)) != PBIT_OK) return st;
-        PBIT_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned) * (size_t)RB * TB, s));
+        const int RB = g->dense.n_pad / 128, TB = T <= 128 ? 1 : T / 128, KS = g->dense.n_pad / 512;
+        const size_t nflags = (size_t)RB * TB * KS;
+        if ((st = cb.alloc(&done, nflags)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned) * nflags, s));
         static const bool stepwise = std::getenv("PBIT_DENSE_STEPWISE") != nullptr;  // force per-step launches
         cudaError_t pe = stepwise ? cudaErrorNotSupported
                                   : launch_dense_persistent(*g, a, t0, t1, b, e, done, g->err, s);

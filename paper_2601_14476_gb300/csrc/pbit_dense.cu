@@ -413,8 +413,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
     const int NT = a.NT;
     uint8_t* sA = smem;                                    // 128 x kSlice bytes, stationary
     uint8_t* sB = sA + kRows * kSlice;                     // NT x kSlice bytes
-    float* part = (float*)(sB + (size_t)NT * kSlice);      // column-major [NT][128]
-    float* s_lam = part + (size_t)NT * kRows;              // per-row parameters
+    // partial fields, column-major [NT][128], two buffers used on alternate steps; they are exact
+    // integers of magnitude <= 16 * 512, so int16 holds them
+    int16_t* part_buf0 = (int16_t*)(sB + (size_t)NT * kSlice);
+    int16_t* part_buf1 = part_buf0 + (size_t)NT * kRows;
+    float* s_lam = (float*)(part_buf1 + (size_t)NT * kRows);  // per-row parameters
     float* s_del = s_lam + kRows;
     uint32_t* s_thr = (uint32_t*)(s_del + kRows);
     int32_t* s_h = (int32_t*)(s_thr + kRows);
@@ -473,7 +476,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
     const int pairs = NT / 2;
     const int pb = (ks * pairs) / a.KS, pe = ((ks + 1) * pairs) / a.KS;
     const int items = (pe - pb) * (kRows / 4);
-    const unsigned* prod0 = pa.done + (size_t)tb * RB + (size_t)kFlagsPerSlice * ks;
+    // progress flags, one per CTA: done[((tb * RB) + rb) * KS + ks] = steps published
+    const unsigned* prod0 = pa.done + ((size_t)tb * RB + (size_t)kFlagsPerSlice * ks) * a.KS;
+    const int nprod = kFlagsPerSlice * a.KS;  // the CTAs that write this CTA's K slice
     const uint32_t idesc = idesc_e4m3((uint32_t)NT);
     const int L = pa.step_end - pa.step_begin;
     // Item `it` = (pair pb + it/32, rows 4*(it%32)..+4).  The thread that
@@ -485,21 +490,25 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
         const int step = pa.step_begin + ls;
         const uint8_t* cur = (ls & 1) ? pa.buf1 : pa.buf0;
         uint8_t* nxt = (ls & 1) ? pa.buf0 : pa.buf1;
+        int16_t* part = (ls & 1) ? part_buf1 : part_buf0;
         if (control) {
-            if (lane == 0 && !s_abort) {
-                bool ok = true;
-                if (ls > 0) {
-                    const long long start = clock64();
-                    for (int f = 0; f < kFlagsPerSlice && ok; ++f) {
-                        while (ld_acquire(prod0 + f) < (unsigned)ls) {
-                            if (clock64() - start > (1ll << 31)) {
-                                ok = false;
-                                break;
-                            }
-                        }
+            bool ok = s_abort == 0;
+            if (ok && ls > 0) {
+                // every lane watches some of the producer flags, so their L2 round trips overlap
+                const long long start = clock64();
+                for (;;) {
+                    bool ready = true;
+                    for (int f = lane; f < nprod; f += 32) ready = ready && ld_acquire(prod0 + f) >= (unsigned)ls;
+                    if (__all_sync(0xFFFFFFFFu, ready)) break;
+                    if (__shfl_sync(0xFFFFFFFFu, (int)(clock64() - start > (1ll << 31)), 0)) {
+                        ok = false;
+                        break;
                     }
-                    fence_proxy_async();
                 }
+                __syncwarp();
+            }
+            if (lane == 0 && s_abort == 0) {
+                if (ls > 0) fence_proxy_async();
                 if (ok) {
                     mbar_expect_tx(&bars[1], (uint32_t)NT * kSlice);
                     bulk_g2s(sB, cur + (size_t)ks * ((size_t)a.T * kSlice) + (size_t)tb * NT * kSlice,
@@ -557,7 +566,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                 tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 16; ++q) part[(size_t)(c + q) * kRows + row] = __uint_as_float(v[q]);
+                for (int q = 0; q < 16; ++q)
+                    part[(size_t)(c + q) * kRows + row] = (int16_t)__float2int_rn(__uint_as_float(v[q]));
             }
         }
         tc_fence_before();
@@ -570,16 +580,16 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                 if (it < items) {
                     const int r0 = (it & 31) * 4;
                     const int lc0 = 2 * (pb + (it >> 5));
-                    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+                    int f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
                     for (int src = 0; src < a.KS; ++src) {
-                        const float* rp = cluster.map_shared_rank(part, src);
-                        const float4 x = *reinterpret_cast<const float4*>(rp + (size_t)lc0 * kRows + r0);
-                        const float4 y = *reinterpret_cast<const float4*>(rp + (size_t)(lc0 + 1) * kRows + r0);
-                        acc0.x += x.x; acc0.y += x.y; acc0.z += x.z; acc0.w += x.w;
-                        acc1.x += y.x; acc1.y += y.y; acc1.z += y.z; acc1.w += y.w;
+                        const int16_t* rp = cluster.map_shared_rank(part, src);
+                        const uint2 x = *reinterpret_cast<const uint2*>(rp + (size_t)lc0 * kRows + r0);
+                        const uint2 y = *reinterpret_cast<const uint2*>(rp + (size_t)(lc0 + 1) * kRows + r0);
+                        f0[0] += (int16_t)(x.x & 0xFFFF); f0[1] += (int16_t)(x.x >> 16);
+                        f0[2] += (int16_t)(x.y & 0xFFFF); f0[3] += (int16_t)(x.y >> 16);
+                        f1[0] += (int16_t)(y.x & 0xFFFF); f1[1] += (int16_t)(y.x >> 16);
+                        f1[2] += (int16_t)(y.y & 0xFFFF); f1[3] += (int16_t)(y.y >> 16);
                     }
-                    const float f0[4] = {acc0.x, acc0.y, acc0.z, acc0.w};
-                    const float f1[4] = {acc1.x, acc1.y, acc1.z, acc1.w};
                     const int t0 = tb * NT + lc0;
                     const int i0 = rb * kRows + r0;
                     const uint32_t old0 = prev0[slot], old1 = prev1[slot];
@@ -594,8 +604,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                                                                 a.instance, a.seed_lo, a.seed_hi);
                             const float lam = s_lam[r], del = s_del[r];
                             const uint32_t thr = s_thr[r];
-                            const int D0 = s_h[r] + __float2int_rn(f0[k]);
-                            const int D1 = s_h[r] + __float2int_rn(f1[k]);
+                            const int D0 = s_h[r] + f0[k];
+                            const int D1 = s_h[r] + f1[k];
                             const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, D0));
                             const uint32_t k1 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, D1));
                             const int s0 = pbit_next(rw.x, rw.y, k0, thr, ((old0 >> (8 * k)) & 0xFF) == kE4m3Plus1 ? 1 : -1);
@@ -611,16 +621,20 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                 }
             }
         }
-        // The cluster barrier orders every CTA's spin stores before the
-        // control thread of rank 0 publishes them device-wide.
-        cluster.sync();
-        if (control) {
-            if (lane == 0 && cluster.block_rank() == 0) {
+        // Publish this CTA's new spins: the epilogue warps meet at a named
+        // barrier (the control warp is not part of it), then one thread makes
+        // their stores visible device-wide and raises the CTA's flag.  No
+        // second cluster barrier: the partial buffers alternate between steps,
+        // and a peer reads this step's buffer before it reaches the next
+        // step's cluster barrier, which this CTA passes before writing the
+        // same buffer again.
+        if (!control) {
+            asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
+            if (tid == 0) {
                 __threadfence();
                 fence_proxy_async();
-                st_release(pa.done + (size_t)tb * RB + rb, (unsigned)(ls + 1));
+                st_release(pa.done + ((size_t)tb * RB + rb) * a.KS + ks, (unsigned)(ls + 1));
             }
-            __syncwarp();
         }
     }
     tc_fence_before();
@@ -632,7 +646,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
 }
 
 size_t persist_smem_bytes(int NT) {
-    return 128 + (size_t)kRows * kSlice + (size_t)NT * kSlice + (size_t)NT * kRows * sizeof(float) +
+    return 128 + (size_t)kRows * kSlice + (size_t)NT * kSlice + 2 * (size_t)NT * kRows * sizeof(int16_t) +
            (size_t)kRows * 16 + (size_t)4 * kEpi * sizeof(uint4) + 64;
 }
 
