@@ -31,6 +31,29 @@ from paper_2601_14476_gb300 import inputs  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
 
+# DRAM bytes per launch of each dominant kernel from one ncu capture (profiles/*.md), valid only while
+# the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
+TRAFFIC = {
+    "dense_persistent_kernel": {"bytes": 5278720 + 327680, "files": ["pbit_dense.cu", "pbit_device.cuh"],
+                                "sha": "6a5d41192297cdbf",
+                                "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
+    "sparse_step_kernel": {"bytes": 21380608 + 256, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
+                           "sha": "61135bf8c79d166a",
+                           "capture": "profiles/sparse_step_kernel_torus100x200_T1024.md"},
+}
+
+
+def traffic_for(kernel: str):
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    m = hashlib.sha256()
+    for f in t["files"]:
+        with open(os.path.join(ROOT, "paper_2601_14476_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return t["bytes"] if m.hexdigest()[:16] == t["sha"] else None
+
 
 def workload(name: str):
     if name == "dense":
@@ -459,7 +482,8 @@ def main():
         achieved = flops / (anneal_ms * 1e-3) / 1e12
         peak = 2.0 * pk["bf16_tflops_sustained"]
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "dense_persistent_kernel",
+                    "frac": achieved / peak, "traffic": traffic_for("dense_persistent_kernel"),
+                    "kernel": "dense_persistent_kernel",
                     "peak_source": f"{pk['source']} bf16 sustained x2 (e4m3 nominal ratio)",
                     "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
     else:
@@ -469,9 +493,11 @@ def main():
         # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
         alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+        kname = "sparse_step_kernel" if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
         roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                    "kernel": "sparse_step_kernel" if chosen == pbit.KERNEL_SPARSE else "resident_kernel",
+                    "frac": achieved / pk["hbm_gbs"],
+                    "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,
+                    "kernel": kname,
                     "peak_source": pk["source"],
                     "per_launch": f"(deg+2) bytes x n*T updates per step; {launches_main} launches"}
     roofline["kernel_ms_per_anneal"] = anneal_ms
