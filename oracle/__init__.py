@@ -24,6 +24,7 @@ _SO = os.path.join(_OUT_DIR, "libpbit_oracle.so")
 _LOCK = threading.Lock()
 _LIB = None
 
+ALG_PSA, ALG_SPSA, ALG_TAPSA = 0, 1, 2
 OFFSET_NORTHSTAR = 0
 OFFSET_LISTING = 1
 OFFSET_EQUATION = 2
@@ -66,6 +67,10 @@ def _lib():
             lib.orc_init_spins.argtypes = [i32, i32, u64, u32, P]
             lib.orc_anneal.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, u64, u32, P, i32, i32, P]
             lib.orc_anneal.restype = C.c_int
+            lib.orc_timing_period.argtypes = [i32, C.c_float]
+            lib.orc_timing_period.restype = i32
+            lib.orc_step_variant.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, u64, u32, i32, f64, i32, i32, P,
+                                             u32, P, P, P, P, P, P]
             _LIB = lib
     return _LIB
 
@@ -211,3 +216,49 @@ def anneal(csr: Csr, sigma0, table, seed: int, instance: int = 0, variability=No
     if rc != 0:
         raise MemoryError("oracle anneal failed")
     return sigma
+
+
+def timing_period(t_res: int, nu_dev: float) -> int:
+    return int(_lib().orc_timing_period(int(t_res), float(nu_dev)))
+
+
+class VariantState:
+    """Per-(node, trial) state of SpSA (last input) and TApSA (last `window` fields)."""
+
+    def __init__(self, n, T, window=4):
+        self.Iprev = np.zeros((n, T), np.float64)
+        self.ring = np.zeros((max(window, 1), n, T), np.int64)
+        self.window = window
+
+
+def step_variant(csr: Csr, sigma, q: int, table, seed: int, instance: int = 0, algorithm: int = ALG_PSA,
+                 stall_prob: float = 0.5, window: int = 4, t_res: int = 0, nu_dev=None, variability=None, h=None,
+                 offset_mode: int = OFFSET_NORTHSTAR, state: VariantState | None = None, want_gap: bool = False):
+    """One sub-step q of pSA / SpSA / TApSA with the optional period timing model; updates `state`."""
+    sigma = _c(sigma, np.int8)
+    T = sigma.shape[1]
+    lam, dlt, pu = _var(variability)
+    state = state or VariantState(csr.n, T, window)
+    out = np.zeros_like(sigma)
+    gap = np.zeros(sigma.shape, np.float64) if want_gap else None
+    tab = _c(table, np.float32)
+    _lib().orc_step_variant(*csr.args(), _p(_c(h, np.int32)), T, _p(lam), _p(dlt), _p(pu), offset_mode, seed,
+                            instance, algorithm, float(stall_prob), int(window), int(t_res),
+                            _p(_c(nu_dev, np.float32)), q & 0xFFFFFFFF, _p(tab), _p(sigma), _p(out),
+                            _p(state.Iprev), _p(state.ring), _p(gap))
+    return (out, gap) if want_gap else out
+
+
+def anneal_variant(csr: Csr, sigma0, table, seed: int, instance: int = 0, algorithm: int = ALG_PSA,
+                   stall_prob: float = 0.5, window: int = 4, t_res: int = 0, nu_dev=None, variability=None,
+                   h=None, offset_mode: int = OFFSET_NORTHSTAR, q_begin: int = 0, q_end: int | None = None,
+                   state: VariantState | None = None):
+    """Sub-steps [q_begin, q_end) (q_end default: len(table) * max(t_res, 1))."""
+    sigma = np.array(sigma0, dtype=np.int8, order="C", copy=True)
+    state = state or VariantState(csr.n, sigma.shape[1], window)
+    if q_end is None:
+        q_end = len(table) * max(t_res, 1)
+    for q in range(q_begin, q_end):
+        sigma = step_variant(csr, sigma, q, table, seed, instance, algorithm, stall_prob, window, t_res, nu_dev,
+                             variability, h, offset_mode, state)
+    return sigma, state

@@ -368,3 +368,90 @@ int orc_anneal(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8
     free(next);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* pSA variants of the Methods section and the paper's timing model.        */
+/*   SpSA  (Eq. SpSA):  with probability p the input keeps I_i(t-1),        */
+/*                      otherwise I_i(t) = I0(t) * (h_i + sum_j J_ij s_j).  */
+/*   TApSA (Eq. TApSA): I_i(t) = I0(t) * (1/alpha) * sum_{k<alpha} TI(t-k), */
+/*                      TI(t) = h_i + sum_j J_ij s_j(t), TI(t < 0) = 0.      */
+/*   Timing (Eq. pbits_variability, T_res): cycle c has T_res sub-steps;    */
+/*   node i updates at sub-step q only when q mod nu_i == 0, with           */
+/*   nu_i = max(1, round(T_res * (1 + nu_dev_i))); I0 is I0(q / T_res).     */
+/* The p-bit then takes x from the input I:                                 */
+/*   NORTHSTAR x = lambda I + I0 delta, LISTING x = lambda (I + I0 delta),  */
+/*   EQUATION x = lambda (I + delta)  (each reduces to the pSA form when    */
+/*   I = I0 D).  Random words: (r, u) as for pSA at counter step q; the     */
+/*   SpSA stall draw is word (trial mod 4) of Philox at counter (node, q,   */
+/*   trial / 4, instance ^ 0x80000000), stall iff its top 24 bits / 2^24 < p.*/
+/* ------------------------------------------------------------------ */
+#define ORC_ALG_PSA 0
+#define ORC_ALG_SPSA 1
+#define ORC_ALG_TAPSA 2
+
+static double orc_stall_draw(uint64_t seed, uint32_t instance, int32_t node, uint32_t step, int32_t trial) {
+    uint32_t ctr[4] = {(uint32_t)node, step, (uint32_t)trial >> 2, instance ^ 0x80000000u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    return (double)(w[trial & 3] >> 8) / 16777216.0;
+}
+
+/* nu_i = max(1, round(T_res * (1 + nu_dev_i))), round half away from zero */
+int32_t orc_timing_period(int32_t t_res, float nu_dev) {
+    double v = round((double)t_res * (1.0 + (double)nu_dev));
+    return v < 1.0 ? 1 : (int32_t)v;
+}
+
+/* One sub-step q of a variant.  State (per node, trial):
+ *   SpSA : Iprev[i*T+t] (double) the last input, 0 before the first step;
+ *   TApSA: ring[(k*n + i)*T + t] (int64) the last `window` fields, slot q mod window.
+ * t_res <= 0 disables the timing model (every node updates every step, I0 = table[q]). */
+void orc_step_variant(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8_t* J, const int32_t* h,
+                      int32_t T, const float* lambda, const float* delta, const float* p_update,
+                      int32_t offset_mode, uint64_t seed, uint32_t instance, int32_t algorithm, double stall_prob,
+                      int32_t window, int32_t t_res, const float* nu_dev, uint32_t q, const float* table,
+                      const int8_t* sigma_in, int8_t* sigma_out, double* Iprev, int64_t* ring, double* gap) {
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t nu = t_res > 0 ? orc_timing_period(t_res, nu_dev ? nu_dev[i] : 0.0f) : 1;
+        const int due = (q % (uint32_t)nu) == 0;
+        const double I0 = (double)table[t_res > 0 ? q / (uint32_t)t_res : q];
+        const double lam = lambda ? (double)lambda[i] : 1.0;
+        const double del = delta ? (double)delta[i] : 0.0;
+        const double p = p_update ? (double)p_update[i] : 1.0;
+        for (int32_t t = 0; t < T; ++t) {
+            const int64_t c = (int64_t)i * T + t;
+            if (!due) {
+                sigma_out[c] = sigma_in[c];
+                if (gap) gap[c] = 1.0; /* no decision */
+                continue;
+            }
+            int64_t D = h ? h[i] : 0;
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) D += (int64_t)J[k] * sigma_in[(int64_t)col[k] * T + t];
+            double I;
+            if (algorithm == ORC_ALG_SPSA) {
+                if (orc_stall_draw(seed, instance, i, q, t) < stall_prob) {
+                    I = Iprev[c];
+                } else {
+                    I = I0 * (double)D;
+                }
+                Iprev[c] = I;
+            } else if (algorithm == ORC_ALG_TAPSA) {
+                ring[((int64_t)(q % (uint32_t)window) * n + i) * T + t] = D;
+                int64_t sum = 0;
+                for (int32_t k = 0; k < window; ++k) sum += ring[((int64_t)k * n + i) * T + t];
+                I = I0 * (double)sum / (double)window;
+            } else {
+                I = I0 * (double)D;
+            }
+            double x;
+            if (offset_mode == ORC_OFFSET_LISTING) x = lam * (I + I0 * del);
+            else if (offset_mode == ORC_OFFSET_EQUATION) x = lam * (I + del);
+            else x = lam * I + I0 * del;
+            orc_draw dr = orc_draw_for(seed, instance, i, q, t);
+            const double g = tanh(x) - dr.r;
+            if (gap) gap[c] = g;
+            sigma_out[c] = (dr.u < p) ? (g > 0.0 ? 1 : -1) : sigma_in[c];
+        }
+    }
+}
