@@ -162,9 +162,29 @@ typedef struct {
     const float* offset;     /* HOST float[n] delta_i, NULL = 0 */
     const float* p_update;   /* HOST float[n] update probability p_i in [0,1], NULL = 1 */
     void* stream;            /* cudaStream_t */
+    /* pSA variants (Methods: Eq. SpSA, Eq. TApSA) and the period timing model (Eq. pbits_variability
+     * with T_res).  The sparse kernel runs them; DENSE and RESIDENT are pSA only. */
+    int32_t algorithm;       /* PBIT_ALG_PSA, PBIT_ALG_SPSA (input kept with probability stall_prob),
+                                PBIT_ALG_TAPSA (input = I0 * mean of the last `window` fields) */
+    float stall_prob;        /* SpSA p in [0,1] (the paper uses 0.5) */
+    int32_t window;          /* TApSA alpha, 1..64 (the paper uses 4) */
+    int32_t t_res;           /* 0: off.  > 0: `steps` counts cycles of t_res sub-steps; node i updates at
+                                sub-step q only when q % nu_i == 0, nu_i = max(1, round(t_res (1 + nu_dev_i)));
+                                I0 = table[q / t_res]; step_begin/step_end then count sub-steps
+                                (step_end 0 = steps * t_res).  The paper uses t_res = 10. */
+    const float* nu_dev;     /* HOST float[n] timing deviations nu_dev_i ~ N(0, s_nu^2), NULL = 0 */
+    void* state;             /* DEVICE variant state of pbit_variant_state_bytes() bytes, read and
+                                written in place so a run can be resumed; NULL = a fresh zero state
+                                (then step_begin must be 0) */
 } pbit_anneal_params;
 
-/* Fill `p` with defaults: T=1, S=1, whole schedule, I0 0.1..10 normalised, NORTHSTAR, AUTO. */
+typedef enum { PBIT_ALG_PSA = 0, PBIT_ALG_SPSA = 1, PBIT_ALG_TAPSA = 2 } pbit_algorithm;
+
+/* Bytes of variant state for n nodes and T trials: SpSA 4*n*T (float32 last input), TApSA
+ * 2*window*n*T (int16 last fields), pSA 0.  Zero-filled memory is the state before step 0. */
+size_t pbit_variant_state_bytes(int32_t n, int32_t trials, int32_t algorithm, int32_t window);
+
+/* Fill `p` with defaults: T=1, S=1, whole schedule, I0 0.1..10 normalised, NORTHSTAR, AUTO, pSA. */
 void pbit_anneal_params_default(pbit_anneal_params* p);
 
 /*
@@ -211,6 +231,15 @@ pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_params* p, const
  * kernel cannot run the shape.
  */
 pbit_status pbit_select_kernel(pbit_graph g, int32_t requested, int32_t trials, int32_t* kernel);
+
+/*
+ * pbit_anneal that also records an observable of the state after every `every`
+ * steps (and after the last step): `what` = 0 energy H, 1 cut.  `trace` is
+ * DEVICE int64[ceil(k/every)][T] for k = step_end - step_begin steps, written
+ * stream-ordered (the paper's energy-vs-cycle curves).
+ */
+pbit_status pbit_anneal_trace(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in, int8_t* spins_out,
+                              int32_t every, int32_t what, int64_t* trace);
 
 /* Write the Philox initial state of (seed, instance) to DEVICE int8[n*T]. */
 pbit_status pbit_init_spins(pbit_graph g, int32_t trials, uint64_t seed, uint32_t instance, int8_t* spins,

@@ -130,8 +130,14 @@ struct CallBuffers {
 };
 
 // Resolve PBIT_KERNEL_AUTO and check a forced kernel against the shape.
-static pbit_status select_kernel(const Graph& g, int requested, int32_t T, int* out) {
+static pbit_status select_kernel(const Graph& g, int requested, int32_t T, int* out, bool variant = false) {
     std::string why;
+    if (variant) {
+        if (requested == PBIT_KERNEL_DENSE || requested == PBIT_KERNEL_RESIDENT)
+            return fail(PBIT_E_UNSUPPORTED, "anneal: SpSA, TApSA and the period timing model run on the sparse kernel");
+        *out = PBIT_KERNEL_SPARSE;
+        return PBIT_OK;
+    }
     if (requested == PBIT_KERNEL_DENSE && !dense_shape_ok(g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
     if (requested == PBIT_KERNEL_RESIDENT && !resident_fits(g, T))
         return fail(PBIT_E_UNSUPPORTED, "anneal: n*T too large for the shared-memory resident kernel");
@@ -343,6 +349,18 @@ void pbit_anneal_params_default(pbit_anneal_params* p) {
     p->i0_normalize = 1;
     p->offset_mode = PBIT_OFFSET_NORTHSTAR;
     p->kernel = PBIT_KERNEL_AUTO;
+    p->algorithm = PBIT_ALG_PSA;
+    p->stall_prob = 0.5f;
+    p->window = 4;
+    p->t_res = 0;
+}
+
+size_t pbit_variant_state_bytes(int32_t n, int32_t trials, int32_t algorithm, int32_t window) {
+    if (n < 1 || trials < 1) return 0;
+    const size_t cells = (size_t)n * (size_t)trials;
+    if (algorithm == PBIT_ALG_SPSA) return 4 * cells;
+    if (algorithm == PBIT_ALG_TAPSA) return 2 * (size_t)(window < 1 ? 1 : window) * cells;
+    return 0;
 }
 
 pbit_status pbit_select_kernel(pbit_graph g, int32_t requested, int32_t trials, int32_t* kernel) {
@@ -368,18 +386,29 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     if (!g || !p || !spins_out) return fail(PBIT_E_INVALID, "anneal: NULL argument");
     if (p->struct_size != sizeof(pbit_anneal_params)) return fail(PBIT_E_INVALID, "anneal: struct_size mismatch");
     const int32_t T = p->trials, S = p->steps;
-    const int32_t b = p->step_begin, e = p->step_end == 0 ? S : p->step_end;
-    if (T < 1 || S < 1 || b < 0 || e < b || e > S) return fail(PBIT_E_INVALID, "anneal: bad trials/steps range");
+    if (p->t_res < 0 || p->t_res > 1000000) return fail(PBIT_E_INVALID, "anneal: bad t_res");
+    const int64_t sub = (int64_t)S * (p->t_res > 0 ? p->t_res : 1);  // schedule length in (sub-)steps
+    if (sub > INT32_MAX) return fail(PBIT_E_INVALID, "anneal: steps * t_res too large");
+    const int32_t b = p->step_begin, e = p->step_end == 0 ? (int32_t)sub : p->step_end;
+    if (T < 1 || S < 1 || b < 0 || e < b || e > sub) return fail(PBIT_E_INVALID, "anneal: bad trials/steps range");
     if ((int64_t)g->n * T > ((int64_t)1 << 40)) return fail(PBIT_E_INVALID, "anneal: n*T too large");
     if (p->offset_mode < 0 || p->offset_mode > 2) return fail(PBIT_E_INVALID, "anneal: bad offset_mode");
     if (p->kernel < 0 || p->kernel > 3) return fail(PBIT_E_INVALID, "anneal: bad kernel");
+    if (p->algorithm < 0 || p->algorithm > 2) return fail(PBIT_E_INVALID, "anneal: bad algorithm");
+    if (p->algorithm == PBIT_ALG_SPSA && !(p->stall_prob >= 0.0f && p->stall_prob <= 1.0f))
+        return fail(PBIT_E_INVALID, "anneal: stall_prob outside [0,1]");
+    if (p->algorithm == PBIT_ALG_TAPSA && (p->window < 1 || p->window > 64))
+        return fail(PBIT_E_INVALID, "anneal: window outside 1..64");
+    const bool is_var = p->algorithm != PBIT_ALG_PSA || p->t_res > 0;
+    if (p->algorithm != PBIT_ALG_PSA && !p->state && b != 0)
+        return fail(PBIT_E_INVALID, "anneal: resuming SpSA/TApSA needs the state buffer of the earlier run");
     pbit_status st = check_device(g);
     if (st != PBIT_OK) return st;
     cudaStream_t s = (cudaStream_t)p->stream;
     const int64_t cells = (int64_t)g->n * T;
 
     int kernel = 0;
-    if ((st = select_kernel(*g, p->kernel, T, &kernel)) != PBIT_OK) return st;
+    if ((st = select_kernel(*g, p->kernel, T, &kernel, is_var)) != PBIT_OK) return st;
 
     // host-side tables
     std::vector<float> tab;
@@ -432,6 +461,31 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         uint32_t* d = nullptr;
         if ((st = cb.put(&d, thr.data(), thr.size())) != PBIT_OK) return st;
         a.par.thr = d;
+    }
+    // variant state and timing periods
+    a.alg = p->algorithm;
+    a.window = p->window < 1 ? 1 : p->window;
+    a.t_res = p->t_res;
+    a.stall_thr = (uint32_t)std::ceil((double)p->stall_prob * 16777216.0);
+    if (p->t_res > 0) {
+        std::vector<int32_t> nu((size_t)g->n);
+        for (int32_t i = 0; i < g->n; ++i) {
+            const double v = std::round((double)p->t_res * (1.0 + (p->nu_dev ? (double)p->nu_dev[i] : 0.0)));
+            nu[(size_t)i] = v < 1.0 ? 1 : (int32_t)std::min(v, 1e9);
+        }
+        int32_t* d = nullptr;
+        if ((st = cb.put(&d, nu.data(), nu.size())) != PBIT_OK) return st;
+        a.nu = d;
+    }
+    if (a.alg != PBIT_ALG_PSA) {
+        const size_t sb = pbit_variant_state_bytes(g->n, T, a.alg, a.window);
+        uint8_t* stt = (uint8_t*)p->state;
+        if (!stt) {
+            if ((st = cb.alloc(&stt, sb)) != PBIT_OK) return st;
+            PBIT_CUDA_TRY(cudaMemsetAsync(stt, 0, sb, s));
+        }
+        if (a.alg == PBIT_ALG_SPSA) a.Iprev = (float*)stt;
+        else a.ring = (int16_t*)stt;
     }
     // the start state
     const int8_t* cur = spins_in;
@@ -506,6 +560,42 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         a.out = dst;
         PBIT_CUDA_TRY(launch_sparse_step(a, s, variant));
         cur = dst;
+    }
+    return PBIT_OK;
+}
+
+pbit_status pbit_anneal_trace(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in, int8_t* spins_out,
+                              int32_t every, int32_t what, int64_t* trace) {
+    if (!g || !p || !spins_out || !trace || every < 1 || what < 0 || what > 1)
+        return fail(PBIT_E_INVALID, "anneal_trace: bad argument");
+    if (p->struct_size != sizeof(pbit_anneal_params)) return fail(PBIT_E_INVALID, "anneal_trace: struct_size");
+    const int64_t sub = (int64_t)p->steps * (p->t_res > 0 ? p->t_res : 1);
+    const int32_t b = p->step_begin, e = p->step_end == 0 ? (int32_t)sub : p->step_end;
+    if (b < 0 || e < b || e > sub) return fail(PBIT_E_INVALID, "anneal_trace: bad step range");
+    cudaStream_t s = (cudaStream_t)p->stream;
+    pbit_anneal_params q = *p;
+    CallBuffers cb;
+    cb.s = s;
+    pbit_status st;
+    if (q.algorithm != PBIT_ALG_PSA && !q.state) {  // one state carried across the segments
+        if (b != 0) return fail(PBIT_E_INVALID, "anneal_trace: resuming needs the state buffer");
+        const size_t sb = pbit_variant_state_bytes(g->n, q.trials, q.algorithm, q.window);
+        uint8_t* stt = nullptr;
+        if ((st = cb.alloc(&stt, sb)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemsetAsync(stt, 0, sb, s));
+        q.state = stt;
+    }
+    const int8_t* in = spins_in;
+    int32_t j = 0;
+    for (int32_t from = b; from < e; from += every, ++j) {
+        q.step_begin = from;
+        q.step_end = std::min(e, from + every);
+        if ((st = pbit_anneal(g, &q, in, spins_out)) != PBIT_OK) return st;
+        in = spins_out;
+        int64_t* row = trace + (size_t)j * (size_t)q.trials;
+        st = what == 0 ? pbit_energy(g, spins_out, q.trials, row, 0, p->stream)
+                       : pbit_cut(g, spins_out, q.trials, row, 0, p->stream);
+        if (st != PBIT_OK) return st;
     }
     return PBIT_OK;
 }

@@ -67,6 +67,14 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int64_t first, uint3
 }
 
 __device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int64_t first, uint32_t* s_tab) {
+    if (is_variant(a)) {
+        if (G == 16) {
+            if (unit) process_tile_variant<16, true>(a, first); else process_tile_variant<16, false>(a, first);
+        } else {
+            if (unit) process_tile_variant<4, true>(a, first); else process_tile_variant<4, false>(a, first);
+        }
+        return;
+    }
     if (G == 16) {
         if (unit) {
             if (table) run_tile<16, true, true>(a, first, s_tab); else run_tile<16, true, false>(a, first, s_tab);
@@ -200,9 +208,17 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     const pbit_anneal_params* p = &pp;
     if (p->struct_size != sizeof(pbit_anneal_params)) return fail(PBIT_E_INVALID, "instance: struct_size mismatch");
     const int32_t T = p->trials, S = p->steps;
-    const int32_t sb = p->step_begin, se = p->step_end == 0 ? S : p->step_end;
-    if (T < 1 || S < 1 || sb < 0 || se < sb || se > S || p->offset_mode < 0 || p->offset_mode > 2)
+    if (p->t_res < 0 || (int64_t)S * (p->t_res > 0 ? p->t_res : 1) > INT32_MAX)
+        return fail(PBIT_E_INVALID, "instance: bad t_res");
+    const int32_t sub = S * (p->t_res > 0 ? p->t_res : 1);
+    const int32_t sb = p->step_begin, se = p->step_end == 0 ? sub : p->step_end;
+    if (T < 1 || S < 1 || sb < 0 || se < sb || se > sub || p->offset_mode < 0 || p->offset_mode > 2)
         return fail(PBIT_E_INVALID, "instance: bad trials/steps/offset mode");
+    if (p->algorithm < 0 || p->algorithm > 2 || (p->algorithm == PBIT_ALG_TAPSA && (p->window < 1 || p->window > 64)) ||
+        (p->algorithm == PBIT_ALG_SPSA && !(p->stall_prob >= 0.0f && p->stall_prob <= 1.0f)))
+        return fail(PBIT_E_INVALID, "instance: bad algorithm parameters");
+    if ((p->algorithm != PBIT_ALG_PSA || p->t_res > 0) && sb != 0)
+        return fail(PBIT_E_INVALID, "instance: variants start at step 0 in batches and servers");
     pbit_status st;
     std::vector<float> tab;
     if ((st = build_schedule(g, p->i0_min, p->i0_max, p->i0_normalize, S, tab)) != PBIT_OK) return st;
@@ -268,6 +284,30 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     if ((st = alloc(&b1, cells)) != PBIT_OK) return st;
     d.buf[0] = (int8_t*)b0;
     d.buf[1] = (int8_t*)b1;
+    // variant state (zero = before step 0) and timing periods
+    a.alg = p->algorithm;
+    a.window = p->window < 1 ? 1 : p->window;
+    a.t_res = p->t_res;
+    a.stall_thr = (uint32_t)std::ceil((double)p->stall_prob * 16777216.0);
+    if (a.alg != PBIT_ALG_PSA) {
+        const size_t sbytes = (a.alg == PBIT_ALG_SPSA ? 4 : 2 * (size_t)a.window) * n * (size_t)T_pad;
+        void* stt = nullptr;
+        if ((st = alloc(&stt, sbytes)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemsetAsync(stt, 0, sbytes, s));
+        if (a.alg == PBIT_ALG_SPSA) a.Iprev = (float*)stt;
+        else a.ring = (int16_t*)stt;
+    }
+    if (p->t_res > 0) {
+        std::vector<uint32_t> nu(n);
+        for (size_t i = 0; i < n; ++i) {
+            const double v = std::round((double)p->t_res * (1.0 + (p->nu_dev ? (double)p->nu_dev[i] : 0.0)));
+            nu[i] = v < 1.0 ? 1u : (uint32_t)std::min(v, 1e9);
+        }
+        void* dp = nullptr;
+        if ((st = alloc(&dp, sizeof(uint32_t) * n)) != PBIT_OK) return st;
+        PBIT_CUDA_TRY(cudaMemcpyAsync(dp, nu.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s));
+        a.nu = (const int32_t*)dp;
+    }
     PBIT_CUDA_TRY(launch_init_spins(g.n, T_pad, p->seed, p->instance, d.buf[0], s));
     d.cur = sb;
     d.end = se;
@@ -296,7 +336,9 @@ pbit_status padded_cuts(pbit_graph g, const InstDesc& d, int64_t* cuts, cudaStre
 size_t inst_bytes(const Graph& g, const pbit_anneal_params& p) {
     const size_t n = (size_t)g.n;
     const size_t T_pad = (size_t)(p.trials + 15) / 16 * 16;
-    return 2 * n * T_pad + sizeof(float) * (size_t)p.steps + 12 * n + 1024;
+    const size_t state = p.algorithm == PBIT_ALG_SPSA ? 4 * n * T_pad
+                         : (p.algorithm == PBIT_ALG_TAPSA ? 2 * (size_t)std::max(1, p.window) * n * T_pad : 0);
+    return 2 * n * T_pad + state + sizeof(float) * (size_t)p.steps + 16 * n + 1024;
 }
 
 template <typename T>
@@ -564,7 +606,7 @@ struct Request {
     uint64_t id = 0;
     pbit_graph g = nullptr;
     pbit_anneal_params p{};
-    std::vector<float> lam, del, pu;
+    std::vector<float> lam, del, pu, nudev;
     size_t bytes = 0;
     Clock::time_point t_submit, t_done;
     int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
@@ -788,6 +830,11 @@ pbit_status pbit_server_submit(pbit_server S, pbit_graph g, const pbit_anneal_pa
         r->pu.assign(p->p_update, p->p_update + n);
         r->p.p_update = r->pu.data();
     }
+    if (p->nu_dev) {
+        r->nudev.assign(p->nu_dev, p->nu_dev + n);
+        r->p.nu_dev = r->nudev.data();
+    }
+    r->p.state = nullptr;
     r->bytes = inst_bytes(*g, *p);
     if (r->bytes > S->budget) return fail(PBIT_E_BUDGET, "server_submit: request needs " +
                                                              std::to_string(r->bytes) + " bytes, budget is " +

@@ -94,6 +94,14 @@ struct StepArgs {
     int32_t T;
     uint32_t seed_lo, seed_hi, instance;
     int32_t offset_mode;
+    // pSA variants and the period timing model (zero: plain pSA)
+    int32_t alg;              // 0 pSA, 1 SpSA, 2 TApSA
+    uint32_t stall_thr;       // SpSA: stall iff (s-word >> 8) < stall_thr = ceil(p * 2^24)
+    int32_t window;           // TApSA window alpha
+    int32_t t_res;            // sub-steps per cycle (0: every node every step, I0 = table[step])
+    const int32_t* nu;        // [n] update period in sub-steps (timing model)
+    float* Iprev;             // SpSA state [n][T]: the last input
+    int16_t* ring;            // TApSA state [window][n][T]: the last fields
 };
 
 // kernels (pbit_sparse.cu)
@@ -108,6 +116,7 @@ struct SparseVariant {
 };
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T);
 cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v = SparseVariant());
+__host__ __device__ inline bool is_variant(const StepArgs& a) { return a.alg != 0 || a.t_res > 0; }
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
 cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
                               cudaStream_t s);

@@ -72,6 +72,8 @@ extern "C" pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_param
     const int32_t b = p->step_begin, e = p->step_end == 0 ? S : p->step_end;
     if (T < 1 || S < 1 || b < 0 || e < b || e > S) return fail(PBIT_E_INVALID, "anneal_noalloc: bad trials/steps range");
     if (p->offset_mode < 0 || p->offset_mode > 2) return fail(PBIT_E_INVALID, "anneal_noalloc: bad offset_mode");
+    if (p->algorithm != PBIT_ALG_PSA || p->t_res > 0)
+        return fail(PBIT_E_UNSUPPORTED, "anneal_noalloc: plain pSA only");
     int device = -1;
     PBIT_CUDA_TRY(cudaGetDevice(&device));
     if (device != gr->device) return fail(PBIT_E_INVALID, "anneal_noalloc: current device is not the graph's device");

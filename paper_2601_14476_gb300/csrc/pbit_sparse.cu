@@ -39,6 +39,20 @@ __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
     process_tile<G, UNIT, TABLE>(a, blockIdx.x * (int64_t)kBlock, s_tab);
 }
 
+template <int G, bool UNIT>
+__global__ void __launch_bounds__(kBlock) sparse_variant_kernel(StepArgs a) {
+    process_tile_variant<G, UNIT>(a, blockIdx.x * (int64_t)kBlock);
+}
+
+template <int G, bool UNIT>
+cudaError_t launch_variant_g(const StepArgs& a, cudaStream_t s) {
+    const int64_t threads = (int64_t)a.n * (a.T / G);
+    const int64_t blocks = (threads + kBlock - 1) / kBlock;
+    sparse_variant_kernel<G, UNIT><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <int G, bool UNIT, bool TABLE>
 cudaError_t launch_step_g(const StepArgs& a, cudaStream_t s) {
     const int64_t threads = (int64_t)a.n * (a.T / G);
@@ -234,6 +248,11 @@ SparseVariant choose_sparse_variant(const Graph& g, int32_t T) {
 cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v) {
     if (v.table && (!a.wabs || !a.tab_off)) v.table = false;
     const int G = group_size(a);
+    if (is_variant(a)) {
+        if (G == 16) return v.unit ? launch_variant_g<16, true>(a, s) : launch_variant_g<16, false>(a, s);
+        if (G == 4) return v.unit ? launch_variant_g<4, true>(a, s) : launch_variant_g<4, false>(a, s);
+        return launch_variant_g<1, false>(a, s);
+    }
     if (G == 16) return launch_step_variant<16>(a, s, v);
     if (G == 4) return launch_step_variant<4>(a, s, v);
     return launch_step_variant<1>(a, s, v);

@@ -213,5 +213,118 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
 }
 
 
+
+// The pSA variants of the Methods section (Eq. SpSA, Eq. TApSA) and the
+// paper's period timing model, one tile as above (no threshold table: the
+// input depends on per-trial state, not on the field alone).
+//   timing: node i updates at sub-step q = a.step only when q % nu_i == 0;
+//           idle nodes copy their spins and leave their state untouched;
+//           I0 = table[q / t_res].
+//   SpSA:   stall draw = word (t % 4) of Philox(node, q, t / 4, instance ^ 2^31);
+//           stalled: I = Iprev, else I = I0 * D; Iprev <- I.
+//   TApSA:  ring[q % window] <- D; I = I0 * (sum of the ring) / window.
+//   x:      NORTHSTAR lambda I + I0 delta, LISTING lambda (I + I0 delta),
+//           EQUATION lambda (I + delta).
+__device__ __forceinline__ float variant_x(int mode, float I0, float lam, float del, float I) {
+    if (mode == 1) return __fmul_rn(lam, __fmaf_rn(I0, del, I));
+    if (mode == 2) return __fmul_rn(lam, __fadd_rn(I, del));
+    return __fmaf_rn(lam, I, __fmul_rn(I0, del));
+}
+
+template <int G, bool UNIT>
+__device__ __forceinline__ void process_tile_variant(const StepArgs& a, int64_t first) {
+    const int groups = a.T / G;
+    const int64_t total = (int64_t)a.n * groups;
+    const int64_t tid = first + threadIdx.x;
+    if (tid >= total) return;
+    const int i = (int)(tid / groups);
+    const int t0 = (int)(tid - (int64_t)i * groups) * G;
+    const uint32_t q = (uint32_t)a.step;
+    uint32_t oldw[Pack<G>::W];
+    load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
+    if (a.t_res > 0 && (q % (uint32_t)__ldg(a.nu + i)) != 0u) {
+        store_group<G>(a.out + (size_t)i * a.T + t0, oldw);
+        return;
+    }
+    const float I0 = __ldg(a.i0_table + (a.t_res > 0 ? q / (uint32_t)a.t_res : q));
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+    int D[G];
+    if constexpr (UNIT && G >= 4) {
+        uint32_t cnt2[Pack<G>::W];
+#pragma unroll
+        for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] = 0;
+        for (int e = rb; e < re; ++e) {
+            const int j = __ldg(a.col + e);
+            const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
+            uint32_t v[Pack<G>::W];
+            load_group<G>(a.in + (size_t)j * a.T + t0, v);
+#pragma unroll
+            for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] += (v[w] & 0x02020202u) ^ flip;
+        }
+        const int deg = re - rb;
+#pragma unroll
+        for (int k = 0; k < G; ++k) D[k] = hi + deg - (int)((cnt2[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+    } else {
+        int acc[G];
+        gather_field<G>(a.row_ptr, a.col, a.J, a.in, a.T, i, t0, acc);
+#pragma unroll
+        for (int k = 0; k < G; ++k) D[k] = hi + acc[k];
+    }
+    float I[G];
+    const size_t base = (size_t)i * a.T + t0;
+    if (a.alg == 1) {
+        uint4 sw = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int t = t0 + k;
+            if (k == 0 || (t & 3) == 0)
+                sw = philox((uint32_t)i, q, (uint32_t)t >> 2, a.instance ^ 0x80000000u, a.seed_lo, a.seed_hi);
+            const uint32_t word = (t & 3) == 0 ? sw.x : ((t & 3) == 1 ? sw.y : ((t & 3) == 2 ? sw.z : sw.w));
+            const bool stall = (word >> 8) < a.stall_thr;
+            I[k] = stall ? a.Iprev[base + k] : __fmul_rn(I0, (float)D[k]);
+            a.Iprev[base + k] = I[k];
+        }
+    } else if (a.alg == 2) {
+        const size_t plane = (size_t)a.n * a.T;
+        const int slot = (int)(q % (uint32_t)a.window);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            a.ring[(size_t)slot * plane + base + k] = (int16_t)D[k];
+            int sum = 0;
+            for (int w = 0; w < a.window; ++w) sum += a.ring[(size_t)w * plane + base + k];
+            I[k] = __fmul_rn(I0, __fdiv_rn((float)sum, (float)a.window));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; ++k) I[k] = __fmul_rn(I0, (float)D[k]);
+    }
+    uint32_t neww[Pack<G>::W];
+#pragma unroll
+    for (int w = 0; w < Pack<G>::W; ++w) neww[w] = 0;
+    if constexpr (G == 1) {
+        const uint4 r = philox((uint32_t)i, q, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
+        const bool odd = t0 & 1;
+        const uint32_t kthr = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[0]));
+        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr, thr, sbyte(oldw[0], 0));
+        neww[0] = (uint32_t)(uint8_t)(int8_t)s;
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k += 2) {
+            const uint4 r = philox((uint32_t)i, q, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo, a.seed_hi);
+            const uint32_t k0 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k]));
+            const uint32_t k1 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k + 1]));
+            const int s0 = pbit_next(r.x, r.y, k0, thr, sbyte(oldw[k >> 2], k & 3));
+            const int s1 = pbit_next(r.z, r.w, k1, thr, sbyte(oldw[k >> 2], (k & 3) + 1));
+            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
+            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
+        }
+    }
+    store_group<G>(a.out + (size_t)i * a.T + t0, neww);
+}
+
 }  // namespace tile
 }  // namespace pbit

@@ -30,6 +30,7 @@ PBIT_GRAPH_DENSE = 1
 
 OFFSET_NORTHSTAR, OFFSET_LISTING, OFFSET_EQUATION = 0, 1, 2
 KERNEL_AUTO, KERNEL_SPARSE, KERNEL_DENSE, KERNEL_RESIDENT = 0, 1, 2, 3
+ALG_PSA, ALG_SPSA, ALG_TAPSA = 0, 1, 2
 
 _STATUS = {0: "PBIT_OK", 1: "PBIT_PENDING", -1: "PBIT_E_INVALID", -2: "PBIT_E_NOMEM", -3: "PBIT_E_CUDA",
            -4: "PBIT_E_TIMEOUT", -5: "PBIT_E_BUDGET", -6: "PBIT_E_UNSUPPORTED", -7: "PBIT_E_NOTFOUND"}
@@ -53,7 +54,8 @@ class pbit_anneal_params(C.Structure):
                 ("i0_max", C.c_double), ("i0_normalize", C.c_int32), ("offset_mode", C.c_int32),
                 ("seed", C.c_uint64), ("instance", C.c_uint32), ("kernel", C.c_int32),
                 ("intensity", C.c_void_p), ("offset", C.c_void_p), ("p_update", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("algorithm", C.c_int32), ("stall_prob", C.c_float),
+                ("window", C.c_int32), ("t_res", C.c_int32), ("nu_dev", C.c_void_p), ("state", C.c_void_p)]
 
 
 class pbit_batch_tuning(C.Structure):
@@ -86,6 +88,8 @@ def _declare(lib):
         "pbit_anneal_params_default": ([_P], None),
         "pbit_anneal": ([_P, _P, _P, _P], C.c_int),
         "pbit_anneal_noalloc": ([_P, _P, _P, _P], C.c_int),
+        "pbit_anneal_trace": ([_P, _P, _P, _P, i32, i32, _P], C.c_int),
+        "pbit_variant_state_bytes": ([i32, i32, i32, i32], C.c_size_t),
         "pbit_init_spins": ([_P, i32, u64, u32, _P, _P], C.c_int),
         "pbit_select_kernel": ([_P, i32, i32, _P], C.c_int),
         "pbit_fields": ([_P, _P, i32, _P, _P], C.c_int),
@@ -223,7 +227,7 @@ def pbit_mean_s(n, src, dst, w) -> float:
 
 def make_params(trials, steps, step_begin=0, step_end=0, i0_min=0.1, i0_max=10.0, i0_normalize=1,
                 offset_mode=OFFSET_NORTHSTAR, seed=1, instance=0, kernel=KERNEL_AUTO, variability=None,
-                stream=None):
+                stream=None, algorithm=ALG_PSA, stall_prob=0.5, window=4, t_res=0, nu_dev=None, state=None):
     """Build a pbit_anneal_params; returns (params, keepalive) - keep both alive during the call."""
     p = pbit_anneal_params()
     lib().pbit_anneal_params_default(C.byref(p))
@@ -238,6 +242,12 @@ def make_params(trials, steps, step_begin=0, step_end=0, i0_min=0.1, i0_max=10.0
             keep.append(arr)
             setattr(p, field, ptr.value if ptr is not None else None)
     p.stream = _stream(stream)
+    p.algorithm, p.stall_prob, p.window, p.t_res = int(algorithm), float(stall_prob), int(window), int(t_res)
+    if nu_dev is not None:
+        arr, ptr = _host(nu_dev, np.float32)
+        keep.append(arr)
+        p.nu_dev = ptr.value
+    p.state = _dev(state)
     return p, keep
 
 
@@ -254,6 +264,16 @@ def pbit_select_kernel(g, requested, trials) -> int:
     out = C.c_int32()
     _check(lib().pbit_select_kernel(g, int(requested), int(trials), C.byref(out)))
     return out.value
+
+
+def pbit_anneal_trace(g, params, spins_in, spins_out, every, what, trace):
+    """`trace`: CUDA int64 tensor [ceil(steps/every), T]; what 0 = energy, 1 = cut."""
+    _check(lib().pbit_anneal_trace(g, C.byref(params), _dev(spins_in), _dev(spins_out), int(every), int(what),
+                                   _dev(trace)))
+
+
+def pbit_variant_state_bytes(n, trials, algorithm, window=4) -> int:
+    return int(lib().pbit_variant_state_bytes(int(n), int(trials), int(algorithm), int(window)))
 
 
 def pbit_init_spins(g, trials, seed, instance, spins, stream=None):

@@ -1,0 +1,130 @@
+"""GPU parity of SpSA (Eq. SpSA), TApSA (Eq. TApSA) and the period timing model
+against the oracle, step by step from the GPU's own state; batch identity and
+the energy trace; the paper's qualitative result that SpSA and TApSA beat
+synchronous pSA."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_14476_gb300 import inputs, pbit
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BAND = 1e-6
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mode=pbit.OFFSET_NORTHSTAR):
+    g = inputs.erdos_renyi_gnm(500, 2500, 3, "pm1")
+    var = inputs.variability(g.n, 3, s_intensity=0.3, s_offset=0.3)
+    G = pbit.Graph.from_inputs(g)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    S = 8 if t_res else steps
+    tab = oracle.schedule(csr, 0.1, 10.0, S)
+    nbytes = pbit.pbit_variant_state_bytes(g.n, T, alg, window)
+    state_dev = torch.zeros(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    spins = oracle.init_spins(g.n, T, 4)
+    ost = oracle.VariantState(g.n, T, window)
+    mismatches = 0
+    for q in range(steps):
+        # the oracle starts each step from the GPU's state
+        if alg == pbit.ALG_SPSA:
+            ost.Iprev[:] = _host(state_dev[:nbytes].view(torch.float32)).reshape(g.n, T)
+        elif alg == pbit.ALG_TAPSA:
+            ost.ring[:] = _host(state_dev[:nbytes].view(torch.int16)).reshape(window, g.n, T)
+        d_in = _dev(spins)
+        d_out = torch.empty_like(d_in)
+        p, keep = pbit.make_params(T, S, step_begin=q, step_end=q + 1, seed=5, variability=var, algorithm=alg,
+                                   stall_prob=stall, window=window, t_res=t_res, nu_dev=nu_dev,
+                                   state=state_dev if nbytes else None, offset_mode=mode)
+        pbit.pbit_anneal(G.handle, p, d_in, d_out)
+        gpu = _host(d_out)
+        want, gap = oracle.step_variant(csr, spins, q, tab, 5, algorithm=alg, stall_prob=stall, window=window,
+                                        t_res=t_res, nu_dev=nu_dev, variability=var, offset_mode=mode, state=ost,
+                                        want_gap=True)
+        bad = gpu != want
+        assert not bad.any() or np.abs(gap[bad]).max() < BAND, q
+        mismatches += int(bad.sum())
+        if alg == pbit.ALG_SPSA:
+            got = _host(state_dev[:nbytes].view(torch.float32)).reshape(g.n, T).astype(np.float64)
+            assert np.allclose(got, ost.Iprev, rtol=2e-7, atol=0), q
+        elif alg == pbit.ALG_TAPSA:
+            got = _host(state_dev[:nbytes].view(torch.int16)).reshape(window, g.n, T)
+            assert np.array_equal(got.astype(np.int64), ost.ring), q
+        spins = gpu
+    return mismatches
+
+
+@pytest.mark.parametrize("mode", [pbit.OFFSET_NORTHSTAR, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+def test_spsa_lockstep(mode):
+    assert _lockstep(pbit.ALG_SPSA, mode=mode) <= 2
+
+
+@pytest.mark.parametrize("T", [32, 12, 5])
+def test_tapsa_lockstep(T):
+    assert _lockstep(pbit.ALG_TAPSA, T=T) <= 2
+
+
+def test_timing_model_lockstep():
+    nu = np.random.default_rng(2).normal(0, 0.5, 500).astype(np.float32)
+    assert _lockstep(pbit.ALG_PSA, steps=30, t_res=10, nu_dev=nu) <= 2
+    assert _lockstep(pbit.ALG_TAPSA, steps=25, t_res=10, nu_dev=nu) <= 2
+
+
+def test_variants_in_batch_equal_alone():
+    gs = [inputs.erdos_renyi_gnm(700, 2100, 1, "+1"), inputs.rgg_knn(900, 2, 3, "pm1"),
+          inputs.torus_2d(20, 25, 3, "pm1")]
+    nu = np.random.default_rng(5).normal(0, 0.3, 900).astype(np.float32)
+    kws = [dict(trials=64, steps=50, seed=1, algorithm=pbit.ALG_SPSA),
+           dict(trials=48, steps=40, seed=2, algorithm=pbit.ALG_TAPSA, window=4),
+           dict(trials=32, steps=6, seed=3, t_res=10, nu_dev=nu[:500], algorithm=pbit.ALG_PSA)]
+    Gs = [pbit.Graph.from_inputs(g) for g in gs]
+    B = pbit.Batch(Gs, kws)
+    B.run(chunk_steps=16)
+    for k, (G, kw) in enumerate(zip(Gs, kws)):
+        out = torch.empty((G.n, kw["trials"]), dtype=torch.int8, device="cuda")
+        p, keep = pbit.make_params(**kw)
+        pbit.pbit_anneal(G.handle, p, None, out)
+        assert np.array_equal(B.spins(k).cpu().numpy(), _host(out)), k
+
+
+def test_energy_trace():
+    g = inputs.erdos_renyi_gnm(800, 19176, 1, "+1")
+    G = pbit.Graph.from_inputs(g)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    T, S, every = 16, 100, 10
+    for alg in (pbit.ALG_PSA, pbit.ALG_TAPSA):
+        trace = torch.zeros((S // every, T), dtype=torch.int64, device="cuda")
+        out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+        p, keep = pbit.make_params(T, S, seed=2, algorithm=alg)
+        pbit.pbit_anneal_trace(G.handle, p, None, out, every, 0, trace)
+        tr = _host(trace)
+        ref = _host(G.anneal(T, S, seed=2, algorithm=alg))
+        assert np.array_equal(_host(out), ref)
+        assert np.array_equal(tr[-1], oracle.energy(csr, ref))
+        # the row after 30 steps equals the energy of a separate 30-step run
+        mid = _host(G.anneal(T, S, step_end=30, seed=2, algorithm=alg)) if alg == pbit.ALG_PSA else None
+        if mid is not None:
+            assert np.array_equal(tr[2], oracle.energy(csr, mid))
+
+
+def test_spsa_and_tapsa_beat_synchronous_psa():
+    """Methods/Results: TApSA and SpSA reach far higher cuts than plain pSA on a G1-shaped graph."""
+    w = inputs.plain_er800()
+    G = pbit.Graph.from_inputs(w.graph)
+    T, S = 64, 1000
+    res = {}
+    for name, kw in (("psa", {}), ("spsa", dict(algorithm=pbit.ALG_SPSA, stall_prob=0.5)),
+                     ("tapsa", dict(algorithm=pbit.ALG_TAPSA, window=4))):
+        out = G.anneal(T, S, seed=3, kernel=pbit.KERNEL_SPARSE, **kw)
+        res[name] = G.cut(out).mean()
+    assert res["spsa"] > 1.5 * res["psa"] + 100 and res["tapsa"] > 1.5 * res["psa"] + 100, res
