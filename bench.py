@@ -65,6 +65,13 @@ def workload(name: str):
     raise SystemExit(f"unknown config {name}")
 
 
+def workload_config(w) -> dict:
+    """The keys that name a single-instance workload, shared by both bench arms."""
+    g = w.graph
+    return {"workload": w.name, "n": g.n, "edges": g.m, "trials": w.trials, "anneal_steps": w.steps,
+            "variability": w.var is not None, "updates_per_step": g.n * w.trials * w.steps}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -95,8 +102,9 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
+            time.sleep(0.3)  # let the sampler start before the timed region
         except Exception:  # noqa: BLE001
             self.proc = None
         return self
@@ -172,7 +180,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": "spin-updates/s", "value": val, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * upd_run / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": {"workload": w.name},
+            "dtype": "f64", "data": "synthetic", "config": workload_config(w),
             "cpu_baseline": {**base, "value": val},
             "e2e": {"value": val, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -193,13 +201,21 @@ def _dist_setup():
     return rank, world, local, dist
 
 
-def _max_over_ranks(dist, x):
+def _max_over_ranks(dist, x, device="cuda"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if not dist:
         return x
     import torch
-    t = torch.tensor([float(x)], device="cuda")
+    t = torch.tensor([float(x)], device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(dist, units_per_rank: float, ms_local: float, world: int, device="cuda"):
+    """Whole-job rate: all ranks' units (each rank runs the same per-rank work: weak scaling)
+    divided by the slowest rank's time.  Returns (value per second, max ms)."""
+    ms = _max_over_ranks(dist, ms_local, device)
+    return world * units_per_rank / (ms * 1e-3), ms
 
 
 def bench_multi(args):
@@ -250,8 +266,7 @@ def bench_multi(args):
                 batched_cuts = [B.cuts(k) for k in range(len(ws))]
                 B.close()
         launches = pbit.pbit_launch_count() - launches0
-        ms = _max_over_ranks(dist, float(np.mean(times)))
-        value = world * upd_run / (ms * 1e-3)
+        value, ms = job_throughput(dist, upd_run, float(np.mean(times)), world)
         # plain form: one instance after another, one launch per step (or one resident launch)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         outs = [torch.empty((w.graph.n, w.trials), dtype=torch.int8, device="cuda") for w in ws]
@@ -385,7 +400,7 @@ def bench_multi(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain", "batch", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window per rate (serve config)")
@@ -454,13 +469,8 @@ def main():
         torch.cuda.synchronize()
     launches = pbit.pbit_launch_count() - launches0
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = float(np.mean(ms))
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
     upd_run = g.n * T * S
-    value = world * upd_run / (ms_step * 1e-3)
+    value, ms_step = job_throughput(dist, upd_run, float(np.mean(ms)), world)
 
     # dominant kernel: the anneal itself (one persistent launch for the dense path, one launch per step
     # otherwise); its average launch duration from CUDA events on the launching stream
@@ -535,11 +545,9 @@ def main():
         "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
-        "config": {"workload": w.name, "n": g.n, "edges": g.m, "trials": T, "anneal_steps": S,
-                   "variability": w.var is not None, "l2": "flushed between timed steps",
+        "config": {**workload_config(w), "l2": "flushed between timed steps",
                    "kernel": {0: "auto", 1: "sparse", 2: "dense", 3: "resident"}[chosen],
-                   "mean_cut": float(host_cuts.mean()),
-                   "updates_per_step": upd_run},
+                   "mean_cut": float(host_cuts.mean())},
         "roofline": roofline,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_val, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),

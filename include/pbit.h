@@ -268,6 +268,15 @@ pbit_status pbit_fields_dense(pbit_graph g, const int8_t* spins, int32_t trials,
 pbit_status pbit_graph_status(pbit_graph g, void* stream);
 
 /*
+ * Exercise the failure path without a fault: one kernel waits for a device
+ * flag that nothing sets, gives up after about budget_us microseconds
+ * (1..2e6), records the timeout in the graph's error word and returns, so a
+ * following pbit_graph_status reports PBIT_E_TIMEOUT and the context stays
+ * usable.  Stream-ordered.
+ */
+pbit_status pbit_selftest_timeout(pbit_graph g, int32_t budget_us, void* stream);
+
+/*
  * Per-trial cut = sum over edges of w * [sigma_src != sigma_dst], and energy
  * H = -sum_i h_i sigma_i - sum_{i<j} J_ij sigma_i sigma_j, exact int64.
  * `out` is HOST int64[T] (the call synchronises `stream`) when out_on_host

@@ -626,6 +626,20 @@ pbit_status pbit_fields_dense(pbit_graph g, const int8_t* spins, int32_t trials,
     return PBIT_OK;
 }
 
+pbit_status pbit_selftest_timeout(pbit_graph g, int32_t budget_us, void* stream) {
+    if (!g || budget_us < 1 || budget_us > 2000000) return fail(PBIT_E_INVALID, "selftest_timeout: budget 1..2e6 us");
+    pbit_status st = check_device(g);
+    if (st != PBIT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* flag = nullptr;
+    PBIT_CUDA_TRY(cudaMallocAsync((void**)&flag, sizeof(unsigned), s));
+    PBIT_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(unsigned), s));
+    cudaError_t e = launch_bounded_wait_selftest(flag, (long long)budget_us * 1000, g->err, s);
+    cudaFreeAsync(flag, s);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest_timeout");
+    return PBIT_OK;
+}
+
 pbit_status pbit_graph_status(pbit_graph g, void* stream) {
     if (!g) return fail(PBIT_E_INVALID, "graph_status: NULL graph");
     pbit_status st = check_device(g);

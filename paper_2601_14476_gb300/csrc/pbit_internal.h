@@ -134,6 +134,7 @@ cudaError_t launch_dense_cut_energy(const Graph& g, const int8_t* spins, int32_t
                                     uint8_t* tiled_scratch, cudaStream_t st);
 cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t* buf0, uint8_t* buf1, int32_t b,
                                     int32_t e, unsigned* done, int* err, cudaStream_t st);
+cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_ns, int* err, cudaStream_t s);
 // resident single-CTA anneal: all steps in one launch, spins in shared memory
 bool resident_fits(const Graph& g, int32_t T);
 cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,

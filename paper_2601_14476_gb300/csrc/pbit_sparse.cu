@@ -32,6 +32,26 @@ __global__ void init_spins_kernel(int32_t n, int32_t T, uint32_t k0, uint32_t k1
     }
 }
 
+// --------------------------------------------------------- failure path ----
+// Waits (bounded by the global nanosecond timer) on a flag that nothing sets,
+// then records the timeout code in the error word and returns: the same exit
+// path every bounded wait of the library takes.
+__global__ void bounded_wait_selftest_kernel(const unsigned* flag, long long budget_ns, int* err) {
+    if (threadIdx.x != 0) return;
+    unsigned long long start, now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(start));
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0u) return;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if ((long long)(now - start) > budget_ns) {
+            atomicExch(err, 5);
+            return;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ step ----
 template <int G, bool UNIT, bool TABLE>
 __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
@@ -256,6 +276,12 @@ cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant 
     if (G == 16) return launch_step_variant<16>(a, s, v);
     if (G == 4) return launch_step_variant<4>(a, s, v);
     return launch_step_variant<1>(a, s, v);
+}
+
+cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_ns, int* err, cudaStream_t s) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(flag, budget_ns, err);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 bool resident_fits(const Graph& g, int32_t T) {

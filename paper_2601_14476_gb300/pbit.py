@@ -95,6 +95,7 @@ def _declare(lib):
         "pbit_fields": ([_P, _P, i32, _P, _P], C.c_int),
         "pbit_fields_dense": ([_P, _P, i32, _P, _P], C.c_int),
         "pbit_graph_status": ([_P, _P], C.c_int),
+        "pbit_selftest_timeout": ([_P, i32, _P], C.c_int),
         "pbit_cut": ([_P, _P, i32, _P, i32, _P], C.c_int),
         "pbit_energy": ([_P, _P, i32, _P, i32, _P], C.c_int),
         "pbit_batch_create": ([i32, _P, _P, _P], C.c_int),
@@ -287,6 +288,10 @@ def pbit_fields(g, spins, trials, fields, stream=None):
 
 def pbit_fields_dense(g, spins, trials, fields, stream=None):
     _check(lib().pbit_fields_dense(g, _dev(spins), int(trials), _dev(fields), _stream(stream)))
+
+
+def pbit_selftest_timeout(g, budget_us, stream=None):
+    _check(lib().pbit_selftest_timeout(g, int(budget_us), _stream(stream)))
 
 
 def pbit_graph_status(g, stream=None):
