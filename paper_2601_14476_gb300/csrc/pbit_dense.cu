@@ -628,13 +628,12 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
         // and a peer reads this step's buffer before it reaches the next
         // step's cluster barrier, which this CTA passes before writing the
         // same buffer again.
+        // The release store is cumulative: it orders every epilogue thread's
+        // stores (ordered before it by the named barrier) before the flag; the
+        // consumer acquires the flag and fences the async proxy before its bulk copy.
         if (!control) {
             asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
-            if (tid == 0) {
-                __threadfence();
-                fence_proxy_async();
-                st_release(pa.done + ((size_t)tb * RB + rb) * a.KS + ks, (unsigned)(ls + 1));
-            }
+            if (tid == 0) st_release(pa.done + ((size_t)tb * RB + rb) * a.KS + ks, (unsigned)(ls + 1));
         }
     }
     tc_fence_before();
