@@ -37,10 +37,25 @@ TRAFFIC = {
     "dense_persistent_kernel": {"bytes": 5278720 + 327680, "files": ["pbit_dense.cu", "pbit_device.cuh"],
                                 "sha": "6a5d41192297cdbf",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
-    "sparse_step_kernel": {"bytes": 21380608 + 256, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
-                           "sha": "61135bf8c79d166a",
-                           "capture": "profiles/sparse_step_kernel_torus100x200_T1024.md"},
+    "sparse_warp_kernel": {"bytes": 21222400 + 0, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
+                           "sha": "da272bfde6ed97f6",
+                           "capture": "profiles/sparse_warp_kernel_torus100x200_T1024.md"},
 }
+
+
+def sparse_tile_kernel(g, T: int) -> str:
+    """Name of the sparse step kernel the library launches for this graph and trial count.
+
+    Same rule as the library's tile choice: the warp-table tile needs unit weights and
+    2 * max degree + 1 lanes per node segment of min(32, T / G) lanes (G = 32 or 16).
+    """
+    deg = int(np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).max()) if g.m else 0
+    if np.all(np.abs(g.w) == 1) and deg <= 15:
+        for G in (32, 16):
+            groups = T // G
+            if T % G == 0 and (groups % 32 == 0 or 32 % groups == 0) and 2 * deg + 1 <= min(32, groups):
+                return "sparse_warp_kernel"
+    return "sparse_step_kernel"
 
 
 def traffic_for(kernel: str):
@@ -503,7 +518,7 @@ def main():
         # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
         alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-        kname = "sparse_step_kernel" if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
+        kname = sparse_tile_kernel(g, T) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
         roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"],
                     "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,

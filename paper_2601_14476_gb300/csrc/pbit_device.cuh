@@ -29,6 +29,34 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Two Philox4x32-10 blocks whose counters differ only in the third word,
+// evaluated side by side (independent instruction streams for the scheduler).
+__device__ __forceinline__ void philox_pair(uint32_t c0, uint32_t c1, uint32_t c2a, uint32_t c2b, uint32_t c3,
+                                            uint32_t k0, uint32_t k1, uint4& ra, uint4& rb) {
+    uint32_t a0 = c0, a1 = c1, a2 = c2a, a3 = c3, b0 = c0, b1 = c1, b2 = c2b, b3 = c3;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t pa0 = (uint64_t)0xD2511F53u * a0, pa1 = (uint64_t)0xCD9E8D57u * a2;
+        const uint64_t pb0 = (uint64_t)0xD2511F53u * b0, pb1 = (uint64_t)0xCD9E8D57u * b2;
+        const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ a1 ^ k0, na2 = (uint32_t)(pa0 >> 32) ^ a3 ^ k1;
+        const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ b1 ^ k0, nb2 = (uint32_t)(pb0 >> 32) ^ b3 ^ k1;
+        a0 = na0;
+        a1 = (uint32_t)pa1;
+        a2 = na2;
+        a3 = (uint32_t)pa0;
+        b0 = nb0;
+        b1 = (uint32_t)pb1;
+        b2 = nb2;
+        b3 = (uint32_t)pb0;
+    }
+    ra = make_uint4(a0, a1, a2, a3);
+    rb = make_uint4(b0, b1, b2, b3);
+}
+
 // The p-bit input x for an exact integer field D (three placements of the
 // offset; see pbit_offset_mode).  Every operation is an explicitly rounded
 // float32 operation, so the value does not depend on compiler contraction.

@@ -102,7 +102,15 @@ struct StepArgs {
     const int32_t* nu;        // [n] update period in sub-steps (timing model)
     float* Iprev;             // SpSA state [n][T]: the last input
     int16_t* ring;            // TApSA state [window][n][T]: the last fields
+    // item -> node for the warp-table tile: node = (item * grp_m) >> grp_s = item / (T / G),
+    // exact for item < 2^31 (filled by set_group_divisor for the G the launcher picks)
+    uint64_t grp_m;
+    int32_t grp_s;
 };
+
+// Fill grp_m / grp_s for division by d = T / G (Granlund-Montgomery: m = floor(2^(32+l) / d) + 1
+// with l = ceil(log2 d); the quotient is exact for every 32-bit dividend below 2^31).
+void set_group_divisor(StepArgs& a, int32_t G);
 
 // kernels (pbit_sparse.cu)
 cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* spins,
@@ -113,6 +121,7 @@ cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t inst
 struct SparseVariant {
     bool unit = false;
     bool table = false;
+    int warp_g = 0;      // trials per thread of the warp-table tile (0: not used); see pbit_tile.cuh
 };
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T);
 cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v = SparseVariant());

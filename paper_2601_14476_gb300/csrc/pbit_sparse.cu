@@ -59,6 +59,13 @@ __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
     process_tile<G, UNIT, TABLE>(a, blockIdx.x * (int64_t)kBlock, s_tab);
 }
 
+// Warp-table tile; the minimum residency keeps five (G = 32) or six (G = 16)
+// blocks per SM, the register budget at which the step ran fastest.
+template <int G>
+__global__ void __launch_bounds__(kBlock, G == 32 ? 5 : 6) sparse_warp_kernel(StepArgs a) {
+    process_tile_warp<G>(a, blockIdx.x * (uint32_t)kBlock);
+}
+
 template <int G, bool UNIT>
 __global__ void __launch_bounds__(kBlock) sparse_variant_kernel(StepArgs a) {
     process_tile_variant<G, UNIT>(a, blockIdx.x * (int64_t)kBlock);
@@ -78,6 +85,17 @@ cudaError_t launch_step_g(const StepArgs& a, cudaStream_t s) {
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
     sparse_step_kernel<G, UNIT, TABLE><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t launch_warp_g(const StepArgs& base, cudaStream_t s) {
+    StepArgs a = base;
+    set_group_divisor(a, G);
+    const int64_t threads = (int64_t)a.n * (a.T / G);
+    const int64_t blocks = (threads + kBlock - 1) / kBlock;
+    sparse_warp_kernel<G><<<(unsigned)blocks, kBlock, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -251,10 +269,27 @@ cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t inst
     return cudaGetLastError();
 }
 
+// Trials per thread of the warp-table tile for T trials (0: the tile does not apply).
+int warp_tile_group(const Graph& g, int32_t T) {
+    if (!g.unit_weights || g.max_degree > 15) return 0;
+    for (const int G : {32, 16}) {
+        if (T % G != 0) continue;
+        const int64_t groups = T / G;
+        if (groups % 32 != 0 && 32 % groups != 0) continue;
+        const int64_t L = groups >= 32 ? 32 : groups;
+        if (2 * (int64_t)g.max_degree + 1 > L) continue;
+        if ((int64_t)g.n * groups >= (int64_t(1) << 31)) continue;
+        return G;
+    }
+    return 0;
+}
+
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T) {
     SparseVariant v;
     static const bool plain = std::getenv("PBIT_SPARSE_PLAIN") != nullptr;  // force the plain variant
     if (plain) return v;
+    static const bool no_warp = std::getenv("PBIT_SPARSE_NOWARP") != nullptr;  // force the block-table tile
+    v.warp_g = no_warp ? 0 : warp_tile_group(g, T);
     const int G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
     v.unit = g.unit_weights && g.max_degree <= 127 && G >= 4;
     // table when its entries stay within shared memory and cost well under one per update
@@ -273,9 +308,25 @@ cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant 
         if (G == 4) return v.unit ? launch_variant_g<4, true>(a, s) : launch_variant_g<4, false>(a, s);
         return launch_variant_g<1, false>(a, s);
     }
+    if (v.warp_g != 0 && G == 16) {  // G == 16: T % 16 == 0 and both buffers 16-byte aligned
+        if (v.warp_g == 32) return launch_warp_g<32>(a, s);
+        return launch_warp_g<16>(a, s);
+    }
     if (G == 16) return launch_step_variant<16>(a, s, v);
     if (G == 4) return launch_step_variant<4>(a, s, v);
     return launch_step_variant<1>(a, s, v);
+}
+
+void set_group_divisor(StepArgs& a, int32_t G) {
+    const uint32_t d = (uint32_t)(a.T / G);
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    // floor(2^(32+l) / d) + 1 < 2^33; with item < 2^31 the 64-bit product cannot overflow
+    const unsigned long long num_hi = 1ull << l;  // 2^(32+l) = num_hi * 2^32
+    const unsigned long long q_hi = num_hi / d, r_hi = num_hi % d;
+    const unsigned long long q_lo = ((r_hi << 32)) / d;  // r_hi < d <= 2^31, so r_hi << 32 fits
+    a.grp_m = (q_hi << 32) + q_lo + 1ull;
+    a.grp_s = 32 + l;
 }
 
 cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_ns, int* err, cudaStream_t s) {

@@ -20,7 +20,16 @@ struct Pack {
 
 template <int G>
 __device__ __forceinline__ void load_group(const int8_t* p, uint32_t (&w)[Pack<G>::W]) {
-    if constexpr (G == 16) {
+    if constexpr (G == 32) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int4 v = *reinterpret_cast<const int4*>(p + 16 * q);
+            w[4 * q] = (uint32_t)v.x;
+            w[4 * q + 1] = (uint32_t)v.y;
+            w[4 * q + 2] = (uint32_t)v.z;
+            w[4 * q + 3] = (uint32_t)v.w;
+        }
+    } else if constexpr (G == 16) {
         const int4 v = *reinterpret_cast<const int4*>(p);
         w[0] = (uint32_t)v.x;
         w[1] = (uint32_t)v.y;
@@ -35,7 +44,12 @@ __device__ __forceinline__ void load_group(const int8_t* p, uint32_t (&w)[Pack<G
 
 template <int G>
 __device__ __forceinline__ void store_group(int8_t* p, const uint32_t (&w)[Pack<G>::W]) {
-    if constexpr (G == 16) {
+    if constexpr (G == 32) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            *reinterpret_cast<int4*>(p + 16 * q) =
+                make_int4((int)w[4 * q], (int)w[4 * q + 1], (int)w[4 * q + 2], (int)w[4 * q + 3]);
+    } else if constexpr (G == 16) {
         *reinterpret_cast<int4*>(p) = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
     } else if constexpr (G == 4) {
         *reinterpret_cast<uint32_t*>(p) = w[0];
@@ -213,6 +227,94 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
 }
 
 
+
+// ------------------------------------------------------------ warp table ----
+// Unit weights (every |J| = 1) and small degree: the threshold table of a
+// node lives in registers of the warp lanes that update it.  A warp covers
+// either part of one node's trials (T / G >= 32 groups per node) or several
+// whole nodes (T / G divides 32), so each node owns a segment of L lanes,
+// L = min(32, T / G).  Lane seg + c holds the negated threshold for the field
+// h_i + deg_i - c (c = 0..2 deg_i, needing 2 deg_i + 1 <= L), and the update
+// with packed count c2 = 2 * #(J_ij s_j = -1) reads it with one shuffle from
+// lane seg + c2 (the field is h_i + deg_i - c2).  No shared memory, no block
+// barrier.
+//
+// Decisions without branches or multiplies: (w >> 8) - kthr is negative
+// exactly when the p-bit draw picks +1 (both sides below 2^25), and
+// (u >> 8) - thr when the node updates; the sign bits of four trials are
+// turned into byte masks with prmt's sign-replicating selectors, and
+//   new = U ? (S ? 0x01 : 0xFF) : old = ((U & ~S) | (~U & old)) | 0x01
+// per byte (every spin byte is 0x01 or 0xFF, so bit 0 is always set).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// byte k of w, zero-extended
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int k) { return prmt(w, 0u, 0x4440u | (uint32_t)k); }
+// byte k = 0xFF where v_k < 0 (as int32), else 0x00
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    const uint32_t lo = prmt(v0, v1, 0x00FBu);  // bytes 0, 1: sign of v0, v1
+    const uint32_t hi = prmt(v2, v3, 0xFB00u);  // bytes 2, 3: sign of v2, v3
+    return prmt(lo, hi, 0x7610u);
+}
+
+template <int G>
+__device__ __forceinline__ void process_tile_warp(const StepArgs& a, uint32_t first) {
+    static_assert(G == 16 || G == 32, "warp-table tile needs 4-word trial groups");
+    constexpr int NW = Pack<G>::W;
+    const uint32_t groups = (uint32_t)a.T / G;
+    const uint32_t total = (uint32_t)a.n * groups;
+    const uint32_t tid = first + threadIdx.x;
+    const bool live = tid < total;
+    const uint32_t item = live ? tid : total - 1;  // dead lanes still feed the shuffles
+    const int i = (int)(((unsigned long long)item * a.grp_m) >> a.grp_s);
+    const int t0 = (int)(item - (uint32_t)i * groups) * G;
+    const int lane = threadIdx.x & 31;
+    const int L = groups >= 32u ? 32 : (int)groups;
+    const int seg = lane & ~(L - 1), ell = lane & (L - 1);
+    const float I0 = __ldg(a.i0_table + a.step);
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+    const int deg = re - rb;
+    const uint32_t negk_lane = 0u - pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + deg - ell));
+    uint32_t cnt2[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) cnt2[w] = 0;
+    for (int e = rb; e < re; ++e) {
+        const int j = __ldg(a.col + e);
+        const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
+        uint32_t v[NW];
+        load_group<G>(a.in + (size_t)j * a.T + t0, v);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) cnt2[w] += (v[w] & 0x02020202u) ^ flip;
+    }
+    uint32_t oldw[NW], neww[NW];
+    load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        uint4 r[2];
+        philox_pair((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + 4 * w) >> 1, (uint32_t)(t0 + 4 * w + 2) >> 1,
+                    a.instance, a.seed_lo, a.seed_hi, r[0], r[1]);
+        uint32_t dr[4], du[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, negk_lane, seg + (int)byte_of(cnt2[w], 2 * h));
+            const uint32_t q1 = __shfl_sync(0xFFFFFFFFu, negk_lane, seg + (int)byte_of(cnt2[w], 2 * h + 1));
+            dr[2 * h] = (r[h].x >> 8) + q0;
+            du[2 * h] = (r[h].y >> 8) - thr;
+            dr[2 * h + 1] = (r[h].z >> 8) + q1;
+            du[2 * h + 1] = (r[h].w >> 8) - thr;
+        }
+        const uint32_t S = sign_bytes(dr[0], dr[1], dr[2], dr[3]);
+        const uint32_t U = sign_bytes(du[0], du[1], du[2], du[3]);
+        neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
+    }
+    if (live) store_group<G>(a.out + (size_t)i * a.T + t0, neww);
+}
 
 // The pSA variants of the Methods section (Eq. SpSA, Eq. TApSA) and the
 // paper's period timing model, one tile as above (no threshold table: the

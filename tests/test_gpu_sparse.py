@@ -261,3 +261,78 @@ def test_kernel_variants_agree(tmp_path):
         res.append(np.load(path))
     for key in res[0].files:
         assert np.array_equal(res[0][key], res[1][key]), key
+
+
+def _warp_tile_applies(g, T):
+    """The launch rule of the warp-table tile: unit weights, 2 max-degree + 1 lanes per node segment."""
+    deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).max() if g.m else 0
+    if np.any(np.abs(g.w) != 1) or deg > 15:
+        return False
+    for G in (32, 16):
+        if T % G:
+            continue
+        groups = T // G
+        if groups % 32 and 32 % groups:
+            continue
+        if 2 * deg + 1 <= min(32, groups):
+            return True
+    return False
+
+
+WARP_CASES = [
+    ("torus7x9_T256", lambda: inputs.torus_2d(7, 9, 5, "pm1"), 256, True, False),    # 2 nodes per warp, ragged
+    ("torus9x11_T512", lambda: inputs.torus_2d(9, 11, 6, "pm1"), 512, True, False),  # G = 32, 2 nodes per warp
+    ("torus6x8_T1024", lambda: inputs.torus_2d(6, 8, 7, "pm1"), 1024, True, True),   # one node per warp, h != 0
+    ("torus5x6_T2048", lambda: inputs.torus_2d(5, 6, 8, "pm1"), 2048, False, False),  # two warps per node, ideal
+    ("rgg300_T1024", lambda: inputs.rgg_knn(300, 9, 3, "pm1"), 1024, True, False),
+]
+
+
+@pytest.mark.parametrize("case", WARP_CASES, ids=[c[0] for c in WARP_CASES])
+def test_warp_tile_lockstep(case):
+    """Warp-table tile (threshold table in lanes, shuffled by packed count) vs the oracle, step by step."""
+    _, make, T, with_var, with_h = case
+    g = make()
+    assert _warp_tile_applies(g, T)
+    var = inputs.variability(g.n, 4, s_intensity=0.3, s_offset=0.3) if with_var else None
+    h = np.random.default_rng(3).integers(-3, 4, g.n).astype(np.int32) if with_h else None
+    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    S = 40
+    tab = oracle.schedule(csr, 0.1, 10.0, S)
+    state = oracle.init_spins(g.n, T, 21, 2)
+    for t in list(range(0, S, 3)) + [S - 1]:
+        d_in = _dev(state)
+        d_out = torch.empty_like(d_in)
+        p, keep = pbit.make_params(T, S, step_begin=t, step_end=t + 1, seed=21, instance=2, variability=var,
+                                   kernel=pbit.KERNEL_SPARSE)
+        pbit.pbit_anneal(G.handle, p, d_in, d_out)
+        gpu = _host(d_out)
+        want, gap = oracle.step(csr, state, t, tab[t], 21, 2, variability=var, h=h, want_gap=True)
+        bad = gpu != want
+        assert not bad.any() or np.abs(gap[bad]).max() < BAND, (t, int(bad.sum()))
+        state = gpu
+
+
+def test_warp_tile_equals_block_tile(tmp_path):
+    """Whole anneals: the warp-table tile gives exactly the block-table tile's spins (forced in a child)."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2601_14476_gb300 import inputs, pbit\n"
+        "outs = []\n"
+        "for g, T in ((inputs.torus_2d(30, 40, 3, 'pm1'), 1024), (inputs.torus_2d(13, 17, 4, 'pm1'), 256),\n"
+        "             (inputs.torus_2d(11, 13, 5, 'pm1'), 512), (inputs.rgg_knn(900, 6, 3, 'pm1'), 2048)):\n"
+        "    G = pbit.Graph.from_inputs(g)\n"
+        "    var = inputs.variability(g.n, 2)\n"
+        "    outs.append(G.anneal(T, 60, seed=9, variability=var, kernel=pbit.KERNEL_SPARSE).cpu().numpy())\n"
+        "np.savez(%r, *outs)\n")
+    res = []
+    for k, extra in enumerate(({}, {"PBIT_SPARSE_NOWARP": "1"})):
+        path = str(tmp_path / f"w{k}.npz")
+        subprocess.run([sys.executable, "-c", code % path], check=True, env=dict(os.environ, **extra), timeout=300)
+        res.append(np.load(path))
+    for key in res[0].files:
+        assert np.array_equal(res[0][key], res[1][key]), key
