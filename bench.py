@@ -37,18 +37,24 @@ TRAFFIC = {
     "dense_persistent_kernel": {"bytes": 5278720 + 327680, "files": ["pbit_dense.cu", "pbit_device.cuh"],
                                 "sha": "6a5d41192297cdbf",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
+    "sparse_flow_kernel": {"bytes": None, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
+                           "sha": "", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
     "sparse_warp_kernel": {"bytes": 21222400 + 0, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
                            "sha": "da272bfde6ed97f6",
                            "capture": "profiles/sparse_warp_kernel_torus100x200_T1024.md"},
 }
 
 
-def sparse_tile_kernel(g, T: int) -> str:
-    """Name of the sparse step kernel the library launches for this graph and trial count.
+def sparse_tile_kernel(g, T: int, steps: int) -> str:
+    """Name of the sparse kernel the library launches for this graph, trial count and step count.
+
+    Two or more plain-pSA steps run in one multi-step launch (unless PBIT_SPARSE_STEPWISE is set).
 
     Same rule as the library's tile choice: the warp-table tile needs unit weights and
     2 * max degree + 1 lanes per node segment of min(32, T / G) lanes (G = 32 or 16).
     """
+    if steps >= 2 and not os.environ.get("PBIT_SPARSE_STEPWISE"):
+        return "sparse_flow_kernel"
     deg = int(np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).max()) if g.m else 0
     if np.all(np.abs(g.w) == 1) and deg <= 15:
         for G in (32, 16):
@@ -67,7 +73,7 @@ def traffic_for(kernel: str):
     for f in t["files"]:
         with open(os.path.join(ROOT, "paper_2601_14476_gb300", "csrc", f), "rb") as fh:
             m.update(fh.read())
-    return t["bytes"] if m.hexdigest()[:16] == t["sha"] else None
+    return t["bytes"] if t["bytes"] is not None and m.hexdigest()[:16] == t["sha"] else None
 
 
 def workload(name: str):
@@ -512,13 +518,13 @@ def main():
                     "peak_source": f"{pk['source']} bf16 sustained x2 (e4m3 nominal ratio)",
                     "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
     else:
-        launches_main = S if chosen == pbit.KERNEL_SPARSE else 1
+        kname = sparse_tile_kernel(g, T, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
+        launches_main = S if kname in ("sparse_warp_kernel", "sparse_step_kernel") else 1
         per_launch_ms = anneal_ms / launches_main
         mean_deg = 2.0 * g.m / g.n
         # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
         alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-        kname = sparse_tile_kernel(g, T) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
         roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"],
                     "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,

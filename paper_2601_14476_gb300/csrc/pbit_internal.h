@@ -35,6 +35,18 @@ struct DenseOperand {
     size_t bytes = 0;
 };
 
+// Tile dependencies of the multi-step sparse kernel for one item count per
+// node (groups = T / G): tile t may run step j once every tile in
+// idx[ptr[t] .. ptr[t+1]) has finished step j - 1; an empty list means "wait
+// for the whole previous step".
+struct FlowDeps {
+    int32_t groups = 0;
+    int32_t ntiles = 0;
+    int32_t* ptr = nullptr;  // device [ntiles + 1]
+    int32_t* idx = nullptr;  // device
+    int64_t listed = 0;      // tiles with their own list (the rest wait for the whole step)
+};
+
 struct Graph {
     int32_t n = 0;
     int64_t n_edges = 0;
@@ -56,6 +68,7 @@ struct Graph {
     int32_t max_wabs = 0;
     bool tab_ok = false;          // prefix sums fit int32
     DenseOperand dense;
+    FlowDeps flow;                // built on first use, for the last groups value asked for
     int* err = nullptr;           // device word: nonzero after a bounded wait gave up
     size_t device_bytes = 0;
     // host copies used by the schedule and the dense builder
@@ -125,6 +138,15 @@ struct SparseVariant {
 };
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T);
 cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v = SparseVariant());
+// Steps [a.step, a.step + k) of plain pSA in one persistent launch: step j reads in0 (j = 0), P (odd j)
+// or Q (even j >= 2) and writes P (even j) or Q (odd j).  Scratch: tile_done [ntiles], step_done [k]
+// and next (zero on entry).  Returns cudaErrorNotSupported when the tile form has no multi-step kernel.
+// The dependency lists are built on the host (and cached in g) under g.mu, held by the caller.
+pbit_status ensure_flow_deps(Graph& g, int32_t T, const int8_t* in0, const int8_t* P, const int8_t* Q,
+                             SparseVariant v);
+cudaError_t launch_sparse_flow(const Graph& g, StepArgs a, int32_t k, const int8_t* in0, int8_t* P, int8_t* Q,
+                               unsigned* tile_done, unsigned* step_done, unsigned long long* next,
+                               SparseVariant v, cudaStream_t s);
 __host__ __device__ inline bool is_variant(const StepArgs& a) { return a.alg != 0 || a.t_res > 0; }
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
 cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,

@@ -336,3 +336,45 @@ def test_warp_tile_equals_block_tile(tmp_path):
         res.append(np.load(path))
     for key in res[0].files:
         assert np.array_equal(res[0][key], res[1][key]), key
+
+
+def test_multistep_flow_equals_stepwise(tmp_path):
+    """One persistent multi-step launch gives exactly the spins of one launch per step (forced in a child).
+
+    Covers the warp-table and block-table tiles, tile dependency lists and whole-step waits (random
+    graph), nodes spanning two tiles (T = 16384), and in-place resumes with odd and even step counts.
+    """
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2601_14476_gb300 import inputs, pbit\n"
+        "outs = []\n"
+        "cases = ((inputs.torus_2d(40, 50, 3, 'pm1'), 1024), (inputs.erdos_renyi_gnm(3000, 9000, 4, '+1'), 64),\n"
+        "         (inputs.rgg_knn(1500, 5, 3, 'pm1'), 16), (inputs.torus_2d(5, 6, 2, 'pm1'), 16384),\n"
+        "         (inputs.complete_pm1(200, 1), 32))\n"
+        "for g, T in cases:\n"
+        "    G = pbit.Graph.from_inputs(g)\n"
+        "    var = inputs.variability(g.n, 2)\n"
+        "    outs.append(G.anneal(T, 57, seed=9, variability=var, kernel=pbit.KERNEL_SPARSE).cpu().numpy())\n"
+        "g = inputs.torus_2d(20, 30, 7, 'pm1')\n"
+        "G = pbit.Graph.from_inputs(g)\n"
+        "a = G.anneal(512, 100, step_end=33, seed=4, kernel=pbit.KERNEL_SPARSE)\n"
+        "for lo, hi in ((33, 60), (60, 100)):\n"
+        "    p, keep = pbit.make_params(512, 100, step_begin=lo, step_end=hi, seed=4, kernel=pbit.KERNEL_SPARSE)\n"
+        "    pbit.pbit_anneal(G.handle, p, a, a)\n"
+        "outs.append(a.cpu().numpy())\n"
+        "torch.cuda.synchronize()\n"
+        "print('launches', pbit.pbit_launch_count())\n"
+        "np.savez(%r, *outs)\n")
+    res, launches = [], []
+    for k, extra in enumerate(({}, {"PBIT_SPARSE_STEPWISE": "1"})):
+        path = str(tmp_path / f"f{k}.npz")
+        r = subprocess.run([sys.executable, "-c", code % path], check=True, env=dict(os.environ, **extra),
+                           timeout=300, capture_output=True, text=True)
+        launches.append(int(r.stdout.split("launches")[-1]))
+        res.append(np.load(path))
+    for key in res[0].files:
+        assert np.array_equal(res[0][key], res[1][key]), key
+    assert launches[0] < launches[1] // 10, launches
