@@ -34,14 +34,12 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of each dominant kernel from one ncu capture (profiles/*.md), valid only while
 # the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
 TRAFFIC = {
-    "dense_persistent_kernel": {"bytes": 5278720 + 327680, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "6a5d41192297cdbf",
+    "dense_persistent_kernel": {"bytes": 4896256 + 176896, "files": ["pbit_dense.cu", "pbit_device.cuh"],
+                                "sha": "bb6c802c447f213d",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
-    "sparse_flow_kernel": {"bytes": None, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
-                           "sha": "", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
-    "sparse_warp_kernel": {"bytes": 21222400 + 0, "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
-                           "sha": "da272bfde6ed97f6",
-                           "capture": "profiles/sparse_warp_kernel_torus100x200_T1024.md"},
+    "sparse_flow_kernel": {"bytes": 24409344 + 167025408,
+                           "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
+                           "sha": "37f8d519b8e9bf0e", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
 }
 
 

@@ -259,18 +259,18 @@ __device__ __forceinline__ uint32_t sign_bytes(uint32_t v0, uint32_t v1, uint32_
     return prmt(lo, hi, 0x7610u);
 }
 
+// One warp's 32 consecutive items: this lane's item is `tid` (tid % 32 == lane).
 template <int G>
-__device__ __forceinline__ void process_tile_warp(const StepArgs& a, uint32_t first) {
+__device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t tid) {
     static_assert(G == 16 || G == 32, "warp-table tile needs 4-word trial groups");
     constexpr int NW = Pack<G>::W;
     const uint32_t groups = (uint32_t)a.T / G;
     const uint32_t total = (uint32_t)a.n * groups;
-    const uint32_t tid = first + threadIdx.x;
     const bool live = tid < total;
     const uint32_t item = live ? tid : total - 1;  // dead lanes still feed the shuffles
     const int i = (int)(((unsigned long long)item * a.grp_m) >> a.grp_s);
     const int t0 = (int)(item - (uint32_t)i * groups) * G;
-    const int lane = threadIdx.x & 31;
+    const int lane = (int)(tid & 31u);
     const int L = groups >= 32u ? 32 : (int)groups;
     const int seg = lane & ~(L - 1), ell = lane & (L - 1);
     const float I0 = __ldg(a.i0_table + a.step);
@@ -314,6 +314,11 @@ __device__ __forceinline__ void process_tile_warp(const StepArgs& a, uint32_t fi
         neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
     }
     if (live) store_group<G>(a.out + (size_t)i * a.T + t0, neww);
+}
+
+template <int G>
+__device__ __forceinline__ void process_tile_warp(const StepArgs& a, uint32_t first) {
+    process_warp_items<G>(a, first + threadIdx.x);  // first is a multiple of the block size
 }
 
 // The pSA variants of the Methods section (Eq. SpSA, Eq. TApSA) and the
