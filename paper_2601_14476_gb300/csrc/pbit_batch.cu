@@ -66,8 +66,9 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int64_t first, uint3
     process_tile<G, UNIT, TABLE>(a, first, s_tab);
 }
 
+template <bool VARIANTS>
 __device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int64_t first, uint32_t* s_tab) {
-    if (is_variant(a)) {
+    if (VARIANTS && is_variant(a)) {
         if (G == 16) {
             if (unit) process_tile_variant<16, true>(a, first); else process_tile_variant<16, false>(a, first);
         } else {
@@ -92,7 +93,11 @@ __device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int
     }
 }
 
-__global__ void __launch_bounds__(kBlock) batch_chunk_kernel(ChunkArgs c) {
+// VARIANTS = false: plain pSA only (the SpSA / TApSA / timing-model tiles are not compiled in,
+// which keeps the register count, and so the residency, of the common case).
+constexpr int kBatchMinBlocks = 8;
+template <bool VARIANTS>
+__global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_chunk_kernel(ChunkArgs c) {
     __shared__ uint32_t s_tab[kTabMax];
     __shared__ unsigned s_item;
     __shared__ int s_ok;
@@ -135,7 +140,7 @@ __global__ void __launch_bounds__(kBlock) batch_chunk_kernel(ChunkArgs c) {
         const int par = (d.parity + k) & 1;
         a.in = d.buf[par];
         a.out = d.buf[par ^ 1];
-        dispatch_tile(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
+        dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
         __threadfence();  // this thread's spin stores, before the tile is counted
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(c.tiles_done + g, 1u);
@@ -176,6 +181,7 @@ struct pbit_batch_s {
     int32_t* d_prefix = nullptr;
     unsigned* d_ctl = nullptr;           // [0] queue, [1..count] tiles_done
     std::vector<void*> allocs;           // per-instance device memory
+    bool variants = false;               // some instance runs SpSA, TApSA or the timing model
     // tuning
     int32_t chunk = 32;
     int32_t ctas_per_sm = 0;             // 0 = occupancy maximum
@@ -313,6 +319,7 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     d.end = se;
     d.parity = 0;
     d.G = T_pad % 16 == 0 ? 16 : 4;
+    set_group_divisor(d.a, d.G);
     d.T_real = T;
     const SparseVariant v = choose_sparse_variant(g, T_pad);
     d.unit = v.unit ? 1 : 0;
@@ -350,10 +357,22 @@ pbit_status dev_alloc(pbit_batch b, T** p, size_t count) {
     return PBIT_OK;
 }
 
+int chunk_occupancy(bool variants) {
+    int occ = 0;
+    if (variants) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel<true>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel<false>, kBlock, 0);
+    return occ;
+}
+
+void launch_chunk(bool variants, int grid, const ChunkArgs& c, cudaStream_t s) {
+    if (variants) batch_chunk_kernel<true><<<grid, kBlock, 0, s>>>(c);
+    else batch_chunk_kernel<false><<<grid, kBlock, 0, s>>>(c);
+}
+
 int grid_for(pbit_batch b) {
-    int sms = 0, occ = 0;
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel, kBlock, 0);
+    int occ = chunk_occupancy(b->variants);
     if (occ < 1) occ = 1;
     const int per = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, occ) : occ;
     return std::max(1, sms * per);
@@ -389,7 +408,7 @@ pbit_status ensure_graph(pbit_batch b, cudaStream_t user) {
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         c.err = b->graphs[0]->err;
-        batch_chunk_kernel<<<grid, kBlock, 0, cap>>>(c);
+        launch_chunk(b->variants, grid, c, cap);
         batch_advance_kernel<<<(b->count + 255) / 256, 256, 0, cap>>>(b->d_inst, b->count, b->chunk, b->d_ctl,
                                                                       b->d_ctl + 1);
         e = cudaStreamEndCapture(cap, &graph);
@@ -443,6 +462,7 @@ pbit_status pbit_batch_create(int32_t count, const pbit_graph* graphs, const pbi
             return fail(PBIT_E_INVALID, "batch_create: bad graph or graphs on different devices at " + std::to_string(k));
         InstDesc& d = b->host_desc[(size_t)k];
         if ((st = build_inst(*g, params[k], s, b->allocs, d, nullptr)) != PBIT_OK) return st;
+        b->variants = b->variants || is_variant(d.a);
         b->tile_prefix[(size_t)k + 1] = b->tile_prefix[(size_t)k] + d.tiles;
     }
     b->total_tiles = b->tile_prefix[(size_t)count];
@@ -707,10 +727,12 @@ void server_loop(pbit_server_s* S) {
         c.queue = S->d_ctl;
         c.tiles_done = S->d_ctl + 1;
         c.err = S->d_err;
-        int sms = 0, occ = 0;
+        bool variants = false;
+        for (int32_t k = 0; k < count; ++k) variants = variants || is_variant(desc[(size_t)k].a);
+        int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel, kBlock, 0);
-        batch_chunk_kernel<<<std::max(1, sms * std::max(1, occ)), kBlock, 0, S->stream>>>(c);
+        const int occ = chunk_occupancy(variants);
+        launch_chunk(variants, std::max(1, sms * std::max(1, occ)), c, S->stream);
         count_launches(1);
         {
             // requests arriving meanwhile are prepared now and join at the next chunk

@@ -83,7 +83,9 @@ cudaError_t launch_variant_g(const StepArgs& a, cudaStream_t s) {
 }
 
 template <int G, bool UNIT, bool TABLE>
-cudaError_t launch_step_g(const StepArgs& a, cudaStream_t s) {
+cudaError_t launch_step_g(const StepArgs& base, cudaStream_t s) {
+    StepArgs a = base;
+    set_group_divisor(a, G);
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
     sparse_step_kernel<G, UNIT, TABLE><<<(unsigned)blocks, kBlock, 0, s>>>(a);
@@ -227,7 +229,7 @@ cudaError_t launch_flow_g(const FlowArgs& f, int device, cudaStream_t s) {
     const unsigned long long items = (unsigned long long)f.k * (unsigned)f.ntiles;
     const unsigned grid = (unsigned)std::min<unsigned long long>(items, (unsigned long long)per_sm[dev] * sms[dev]);
     FlowArgs ff = f;
-    if constexpr (WARP) set_group_divisor(ff.a, G);
+    set_group_divisor(ff.a, G);
     sparse_flow_kernel<G, WARP, UNIT, TABLE><<<grid, kBlock, 0, s>>>(ff);
     count_launches(1);
     return cudaGetLastError();
@@ -442,6 +444,11 @@ cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant 
 
 void set_group_divisor(StepArgs& a, int32_t G) {
     const uint32_t d = (uint32_t)(a.T / G);
+    if (d == 0 || (int64_t)a.n * d + 2 * kBlock >= (int64_t(1) << 31)) {  // items must stay below 2^31
+        a.grp_m = 0;
+        a.grp_s = 0;
+        return;
+    }
     int l = 0;
     while ((1ull << l) < d) ++l;
     // floor(2^(32+l) / d) + 1 < 2^33; with item < 2^31 the 64-bit product cannot overflow

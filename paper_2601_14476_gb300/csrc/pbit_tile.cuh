@@ -130,97 +130,133 @@ __device__ __forceinline__ void decide_group(const StepArgs& a, int i, int t0, c
 // as the direct path, so both give identical decisions.
 constexpr int kTabMax = 4096;  // threshold entries per block (16 KB)
 
+// Byte helpers for the sign-test decisions (see the warp-table tile below).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// byte k of w, zero-extended
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int k) { return prmt(w, 0u, 0x4440u | (uint32_t)k); }
+// byte k = 0xFF where v_k < 0 (as int32), else 0x00
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    const uint32_t lo = prmt(v0, v1, 0x00FBu);  // bytes 0, 1: sign of v0, v1
+    const uint32_t hi = prmt(v2, v3, 0xFB00u);  // bytes 2, 3: sign of v2, v3
+    return prmt(lo, hi, 0x7610u);
+}
+
+// One warp's 32 consecutive items: this lane's item is `tid` (tid % 32 == lane).
 // One tile = kBlock consecutive (node, trial-group) items starting at item
 // `first`, processed by the kBlock threads of the calling block.  s_tab is
 // shared memory of kTabMax entries (TABLE only).  Every thread of the block
 // must call this (the table build has a block barrier).
+// item -> node: the host-computed multiply-shift when the launcher set one (items below 2^31),
+// else 64-bit division
+__device__ __forceinline__ int node_of_item(const StepArgs& a, int64_t item, int groups) {
+    if (a.grp_m != 0ull) return (int)(((unsigned long long)item * a.grp_m) >> a.grp_s);
+    return (int)(item / groups);
+}
+
 template <int G, bool UNIT, bool TABLE>
 __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, uint32_t* s_tab) {
     const int groups = a.T / G;
     const int64_t total = (int64_t)a.n * groups;
     const int64_t tid = first + threadIdx.x;
     const float I0 = __ldg(a.i0_table + a.step);
-    int tab_base = 0, i_first = 0;
+    int tab_base = 0;
     if constexpr (TABLE) {
-        i_first = (int)(first / groups);
-        const int i_last = (int)(min(total - 1, first + kBlock - 1) / groups);
+        // W_i + 1 entries per node of the tile: with few nodes (many trials per node) warp w fills
+        // nodes i_first + w, i_first + w + 8, ... lane by lane; with many nodes each thread fills one
+        const int i_first = node_of_item(a, first, groups);
+        const int i_last = node_of_item(a, min(total - 1, first + kBlock - 1), groups);
         tab_base = __ldg(a.tab_off + i_first);
-        const int cnt = __ldg(a.tab_off + i_last + 1) - tab_base;
-        for (int e = threadIdx.x; e < cnt; e += kBlock) {
-            // node of entry e: the last i in [i_first, i_last] with tab_off[i] - base <= e
-            int lo = i_first, hi = i_last;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(a.tab_off + mid) - tab_base <= e) lo = mid; else hi = mid - 1;
-            }
-            const int node = lo;
-            const int idx = e - (__ldg(a.tab_off + node) - tab_base);
+        const bool by_warp = i_last - i_first < 8;
+        const int lanes = by_warp ? 32 : 1;
+        const int sub = by_warp ? (int)(threadIdx.x & 31) : 0;
+        const int stride = by_warp ? kBlock / 32 : kBlock;
+        for (int node = i_first + (by_warp ? (int)(threadIdx.x >> 5) : (int)threadIdx.x); node <= i_last;
+             node += stride) {
+            const int off = __ldg(a.tab_off + node) - tab_base;
             const int W = __ldg(a.wabs + node);
             const int hi_n = a.h ? __ldg(a.h + node) : 0;
             const float lam = a.par.lambda ? __ldg(a.par.lambda + node) : 1.0f;
             const float del = a.par.delta ? __ldg(a.par.delta + node) : 0.0f;
-            s_tab[e] = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi_n - W + 2 * idx));
+            for (int idx = sub; idx <= W; idx += lanes)
+                s_tab[off + idx] = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi_n - W + 2 * idx));
         }
         __syncthreads();
     }
     if (tid >= total) return;
-    const int i = (int)(tid / groups);
+    const int i = node_of_item(a, tid, groups);
     const int t0 = (int)(tid - (int64_t)i * groups) * G;
     const int hi = a.h ? __ldg(a.h + i) : 0;
     const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
     const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
     const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
     const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+    constexpr int NW = Pack<G>::W;
+    const int deg = re - rb;
 
-    int D[G];  // exact fields, h included
+    // UNIT: packed counts c2 = 2 * #(J_ij s_j = -1) per trial byte, field = h + deg - c2;
+    // otherwise exact fields acc (without h)
+    uint32_t cnt2[UNIT && G >= 4 ? NW : 1];
+    int acc[UNIT && G >= 4 ? 1 : G];
     if constexpr (UNIT && G >= 4) {
-        uint32_t cnt2[Pack<G>::W];
 #pragma unroll
-        for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] = 0;
+        for (int w = 0; w < NW; ++w) cnt2[w] = 0;
         for (int e = rb; e < re; ++e) {
             const int j = __ldg(a.col + e);
             const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
-            uint32_t v[Pack<G>::W];
+            uint32_t v[NW];
             load_group<G>(a.in + (size_t)j * a.T + t0, v);
 #pragma unroll
-            for (int w = 0; w < Pack<G>::W; ++w) cnt2[w] += (v[w] & 0x02020202u) ^ flip;
+            for (int w = 0; w < NW; ++w) cnt2[w] += (v[w] & 0x02020202u) ^ flip;
         }
-        const int deg = re - rb;
-#pragma unroll
-        for (int k = 0; k < G; ++k) D[k] = hi + deg - (int)((cnt2[k >> 2] >> (8 * (k & 3))) & 0xFFu);
     } else {
-        int acc[G];
         gather_field<G>(a.row_ptr, a.col, a.J, a.in, a.T, i, t0, acc);
-#pragma unroll
-        for (int k = 0; k < G; ++k) D[k] = hi + acc[k];
     }
-    int tab_off_i = 0, W_i = 0;
+    // table row of node i; for UNIT the entry of count c2 is row[W_i - c2 / 2] (W_i = deg)
+    const uint32_t* row = nullptr;
+    int W_i = 0;
     if constexpr (TABLE) {
-        tab_off_i = __ldg(a.tab_off + i) - tab_base;
+        row = s_tab + (__ldg(a.tab_off + i) - tab_base);
         W_i = __ldg(a.wabs + i);
     }
-    auto kthr_of = [&](int Dk) -> uint32_t {
-        if constexpr (TABLE) return s_tab[tab_off_i + ((Dk - hi + W_i) >> 1)];
-        else return pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, Dk));
+    auto kthr_at = [&](int k) -> uint32_t {
+        if constexpr (UNIT && G >= 4) {
+            const int c2 = (int)byte_of(cnt2[k >> 2], k & 3);
+            if constexpr (TABLE) return row[W_i - (c2 >> 1)];
+            else return pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + deg - c2));
+        } else {
+            if constexpr (TABLE) return row[(acc[k] + W_i) >> 1];
+            else return pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k]));
+        }
     };
-    uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
+    uint32_t oldw[NW], neww[NW];
     load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
-#pragma unroll
-    for (int w = 0; w < Pack<G>::W; ++w) neww[w] = 0;
     if constexpr (G == 1) {
         const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
         const bool odd = t0 & 1;
-        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr_of(D[0]), thr, sbyte(oldw[0], 0));
+        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr_at(0), thr, sbyte(oldw[0], 0));
         neww[0] = (uint32_t)(uint8_t)(int8_t)s;
     } else {
+        // sign tests and byte masks as in the warp-table tile
 #pragma unroll
-        for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo,
-                                   a.seed_hi);
-            const int s0 = pbit_next(r.x, r.y, kthr_of(D[k]), thr, sbyte(oldw[k >> 2], k & 3));
-            const int s1 = pbit_next(r.z, r.w, kthr_of(D[k + 1]), thr, sbyte(oldw[k >> 2], (k & 3) + 1));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
+        for (int w = 0; w < NW; ++w) {
+            uint4 r[2];
+            philox_pair((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + 4 * w) >> 1, (uint32_t)(t0 + 4 * w + 2) >> 1,
+                        a.instance, a.seed_lo, a.seed_hi, r[0], r[1]);
+            uint32_t dr[4], du[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                dr[2 * h] = (r[h].x >> 8) - kthr_at(4 * w + 2 * h);
+                du[2 * h] = (r[h].y >> 8) - thr;
+                dr[2 * h + 1] = (r[h].z >> 8) - kthr_at(4 * w + 2 * h + 1);
+                du[2 * h + 1] = (r[h].w >> 8) - thr;
+            }
+            const uint32_t S = sign_bytes(dr[0], dr[1], dr[2], dr[3]);
+            const uint32_t U = sign_bytes(du[0], du[1], du[2], du[3]);
+            neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
         }
     }
     store_group<G>(a.out + (size_t)i * a.T + t0, neww);
@@ -245,21 +281,6 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
 // turned into byte masks with prmt's sign-replicating selectors, and
 //   new = U ? (S ? 0x01 : 0xFF) : old = ((U & ~S) | (~U & old)) | 0x01
 // per byte (every spin byte is 0x01 or 0xFF, so bit 0 is always set).
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-// byte k of w, zero-extended
-__device__ __forceinline__ uint32_t byte_of(uint32_t w, int k) { return prmt(w, 0u, 0x4440u | (uint32_t)k); }
-// byte k = 0xFF where v_k < 0 (as int32), else 0x00
-__device__ __forceinline__ uint32_t sign_bytes(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
-    const uint32_t lo = prmt(v0, v1, 0x00FBu);  // bytes 0, 1: sign of v0, v1
-    const uint32_t hi = prmt(v2, v3, 0xFB00u);  // bytes 2, 3: sign of v2, v3
-    return prmt(lo, hi, 0x7610u);
-}
-
-// One warp's 32 consecutive items: this lane's item is `tid` (tid % 32 == lane).
 template <int G>
 __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t tid) {
     static_assert(G == 16 || G == 32, "warp-table tile needs 4-word trial groups");
