@@ -37,10 +37,22 @@ TRAFFIC = {
     "dense_persistent_kernel": {"bytes": 4896256 + 176896, "files": ["pbit_dense.cu", "pbit_device.cuh"],
                                 "sha": "bb6c802c447f213d",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
-    "sparse_flow_kernel": {"bytes": 24409344 + 167025408,
+    "sparse_flow_kernel": {"bytes": 23933952 + 166513920,
                            "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
-                           "sha": "37f8d519b8e9bf0e", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
+                           "sha": "d0d85cb7e7a5e002", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
+    # per launch of a 64-step chunk of all 64 instances
+    "batch_chunk_kernel": {"bytes": 810057216 + 1345518000, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
+                           "sha": "5403f544286cce7e", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
 }
+
+
+def batch_traffic(tuning, steps: int):
+    """DRAM bytes of one batched run (steps / chunk launches), from the per-chunk capture."""
+    per_chunk = traffic_for("batch_chunk_kernel")
+    chunk = TRAFFIC["batch_chunk_kernel"]["chunk_steps"]
+    if per_chunk is None or tuning.get("chunk_steps") != chunk or steps % chunk:
+        return None
+    return per_chunk * (steps // chunk)
 
 
 def sparse_tile_kernel(g, T: int, steps: int) -> str:
@@ -325,7 +337,8 @@ def bench_multi(args):
                        "batched_over_plain": plain_ms / ms, "cuts_identical_to_plain": bool(same),
                        "mean_cut_batched": mean_b, "mean_cut_plain": mean_p},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel": "batch_chunk_kernel",
+                         "frac": achieved / pk["hbm_gbs"], "traffic": batch_traffic(tuning, ws[0].steps),
+                         "kernel": "batch_chunk_kernel",
                          "peak_source": pk["source"],
                          "per_launch": "sum over instances of (deg+2) bytes x n*T updates per step"},
             "cpu_baseline": None,
