@@ -74,3 +74,24 @@ def test_batch_resume_from_given_state_matches_oracle():
     want = oracle.anneal(csr, start, tab, 4, 0, variability=var, step_begin=25)
     # decisions may differ only inside the 1e-6 tie band; over 15 steps x 19200 decisions none is expected
     assert (got != want).mean() < 1e-3
+
+
+def test_batch64_smallest_instances_match_oracle():
+    """The two smallest instances of the 64-instance workload, run inside the whole batch for all 2000
+    steps: per-trial cuts equal the oracle's except trials a tie-band decision diverged, mean within 0.5 %."""
+    ws = inputs.batch64(seed=1, steps=2000)
+    Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+    B = pbit.Batch(Gs, [dict(trials=w.trials, steps=w.steps, seed=w.seed, instance=w.instance,
+                             variability=w.var) for w in ws])
+    B.run()
+    for k in sorted(range(len(ws)), key=lambda k: ws[k].graph.n * ws[k].trials)[:2]:
+        w = ws[k]
+        g = w.graph
+        csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+        tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
+        ref = oracle.anneal(csr, oracle.init_spins(g.n, w.trials, w.seed, w.instance), tab, w.seed, w.instance,
+                            variability=w.var)
+        ref_cut = oracle.cut(g.src, g.dst, g.w, ref)
+        got = B.cuts(k)
+        assert (got == ref_cut).mean() >= 0.75, (k, got, ref_cut)
+        assert abs(got.mean() - ref_cut.mean()) <= 0.005 * abs(ref_cut.mean())
