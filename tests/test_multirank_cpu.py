@@ -44,3 +44,17 @@ def test_job_throughput_two_ranks_gloo():
     for rank, value, ms in res:
         assert ms == pytest.approx(20.0)
         assert value == pytest.approx(2 * 1.0e9 / 0.020)
+
+
+def test_cpu_baseline_single_and_all_cores():
+    """The bench's oracle baseline: a single-thread rate, and every host core running the same bounded
+    sample in its own spawned process."""
+    import os
+
+    import bench
+    from paper_2601_14476_gb300 import inputs
+
+    b = bench.cpu_baseline(inputs.plain_er800(), budget_s=0.2, kind="plain")
+    assert b["kind"] == "oracle" and b["cores"] == 1 and b["value"] > 0
+    if (os.cpu_count() or 1) > 1:
+        assert b["all_cores"]["cores"] == os.cpu_count() and b["all_cores"]["value"] > 0
