@@ -126,7 +126,10 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # raw samples: PBIT_BENCH_OUT if set, else the system temporary directory
+        import tempfile
+        out_dir = os.environ.get("PBIT_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{device_index}.csv")
 
     def __enter__(self):
         try:

@@ -134,7 +134,7 @@ pbit_status pbit_mean_s(int32_t n, int64_t n_edges, const int32_t* src, const in
 /* ------------------------------------------------------------------------ */
 
 typedef enum {
-    PBIT_OFFSET_NORTHSTAR = 0, /* x = I0 * (lambda*D + delta) */
+    PBIT_OFFSET_SCALED = 0, /* x = I0 * (lambda*D + delta) */
     PBIT_OFFSET_LISTING = 1,   /* x = lambda * I0 * (D + delta)   (the paper's pseudo code) */
     PBIT_OFFSET_EQUATION = 2   /* x = lambda * (I0*D + delta)     (Eq. 6 with Eq. 3) */
 } pbit_offset_mode;
@@ -184,7 +184,7 @@ typedef enum { PBIT_ALG_PSA = 0, PBIT_ALG_SPSA = 1, PBIT_ALG_TAPSA = 2 } pbit_al
  * 2*window*n*T (int16 last fields), pSA 0.  Zero-filled memory is the state before step 0. */
 size_t pbit_variant_state_bytes(int32_t n, int32_t trials, int32_t algorithm, int32_t window);
 
-/* Fill `p` with defaults: T=1, S=1, whole schedule, I0 0.1..10 normalised, NORTHSTAR, AUTO, pSA. */
+/* Fill `p` with defaults: T=1, S=1, whole schedule, I0 0.1..10 normalised, SCALED, AUTO, pSA. */
 void pbit_anneal_params_default(pbit_anneal_params* p);
 
 /*

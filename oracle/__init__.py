@@ -25,7 +25,7 @@ _LOCK = threading.Lock()
 _LIB = None
 
 ALG_PSA, ALG_SPSA, ALG_TAPSA = 0, 1, 2
-OFFSET_NORTHSTAR = 0
+OFFSET_SCALED = 0
 OFFSET_LISTING = 1
 OFFSET_EQUATION = 2
 
@@ -178,7 +178,7 @@ def _var(v):
 
 
 def step(csr: Csr, sigma, step_idx: int, I0: float, seed: int, instance: int = 0, variability=None, h=None,
-         offset_mode: int = OFFSET_NORTHSTAR, want_gap: bool = False):
+         offset_mode: int = OFFSET_SCALED, want_gap: bool = False):
     sigma = _c(sigma, np.int8)
     T = sigma.shape[1]
     lam, dlt, pu = _var(variability)
@@ -190,7 +190,7 @@ def step(csr: Csr, sigma, step_idx: int, I0: float, seed: int, instance: int = 0
 
 
 def step_sampled(csr: Csr, sigma, nodes, trials, step_idx: int, I0: float, seed: int, instance: int = 0,
-                 variability=None, h=None, offset_mode: int = OFFSET_NORTHSTAR):
+                 variability=None, h=None, offset_mode: int = OFFSET_SCALED):
     sigma = _c(sigma, np.int8)
     T = sigma.shape[1]
     nodes, trials = _c(nodes, np.int32), _c(trials, np.int32)
@@ -204,7 +204,7 @@ def step_sampled(csr: Csr, sigma, nodes, trials, step_idx: int, I0: float, seed:
 
 
 def anneal(csr: Csr, sigma0, table, seed: int, instance: int = 0, variability=None, h=None,
-           offset_mode: int = OFFSET_NORTHSTAR, step_begin: int = 0, step_end: int | None = None) -> np.ndarray:
+           offset_mode: int = OFFSET_SCALED, step_begin: int = 0, step_end: int | None = None) -> np.ndarray:
     sigma = np.array(sigma0, dtype=np.int8, order="C", copy=True)
     T = sigma.shape[1]
     table = _c(table, np.float32)
@@ -233,7 +233,7 @@ class VariantState:
 
 def step_variant(csr: Csr, sigma, q: int, table, seed: int, instance: int = 0, algorithm: int = ALG_PSA,
                  stall_prob: float = 0.5, window: int = 4, t_res: int = 0, nu_dev=None, variability=None, h=None,
-                 offset_mode: int = OFFSET_NORTHSTAR, state: VariantState | None = None, want_gap: bool = False):
+                 offset_mode: int = OFFSET_SCALED, state: VariantState | None = None, want_gap: bool = False):
     """One sub-step q of pSA / SpSA / TApSA with the optional period timing model; updates `state`."""
     sigma = _c(sigma, np.int8)
     T = sigma.shape[1]
@@ -251,7 +251,7 @@ def step_variant(csr: Csr, sigma, q: int, table, seed: int, instance: int = 0, a
 
 def anneal_variant(csr: Csr, sigma0, table, seed: int, instance: int = 0, algorithm: int = ALG_PSA,
                    stall_prob: float = 0.5, window: int = 4, t_res: int = 0, nu_dev=None, variability=None,
-                   h=None, offset_mode: int = OFFSET_NORTHSTAR, q_begin: int = 0, q_end: int | None = None,
+                   h=None, offset_mode: int = OFFSET_SCALED, q_begin: int = 0, q_end: int | None = None,
                    state: VariantState | None = None):
     """Sub-steps [q_begin, q_end) (q_end default: len(table) * max(t_res, 1))."""
     sigma = np.array(sigma0, dtype=np.int8, order="C", copy=True)

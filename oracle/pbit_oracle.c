@@ -57,7 +57,7 @@
 #define ORC_E_NOMEM (-2)
 
 /* offset placement readings (design notes): */
-#define ORC_OFFSET_NORTHSTAR 0 /* x = I0 * (lambda*D + delta)  */
+#define ORC_OFFSET_SCALED 0 /* x = I0 * (lambda*D + delta)  */
 #define ORC_OFFSET_LISTING 1   /* x = lambda * I0 * (D + delta) */
 #define ORC_OFFSET_EQUATION 2  /* x = lambda * (I0*D + delta)  */
 
@@ -379,7 +379,7 @@ int orc_anneal(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8
 /*   node i updates at sub-step q only when q mod nu_i == 0, with           */
 /*   nu_i = max(1, round(T_res * (1 + nu_dev_i))); I0 is I0(q / T_res).     */
 /* The p-bit then takes x from the input I:                                 */
-/*   NORTHSTAR x = lambda I + I0 delta, LISTING x = lambda (I + I0 delta),  */
+/*   SCALED x = lambda I + I0 delta, LISTING x = lambda (I + I0 delta),  */
 /*   EQUATION x = lambda (I + delta)  (each reduces to the pSA form when    */
 /*   I = I0 D).  Random words: (r, u) as for pSA at counter step q; the     */
 /*   SpSA stall draw is word (trial mod 4) of Philox at counter (node, q,   */

@@ -349,7 +349,7 @@ void pbit_anneal_params_default(pbit_anneal_params* p) {
     p->i0_min = 0.1;
     p->i0_max = 10.0;
     p->i0_normalize = 1;
-    p->offset_mode = PBIT_OFFSET_NORTHSTAR;
+    p->offset_mode = PBIT_OFFSET_SCALED;
     p->kernel = PBIT_KERNEL_AUTO;
     p->algorithm = PBIT_ALG_PSA;
     p->stall_prob = 0.5f;

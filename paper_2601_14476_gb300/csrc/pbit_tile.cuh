@@ -351,7 +351,7 @@ __device__ __forceinline__ void process_tile_warp(const StepArgs& a, uint32_t fi
 //   SpSA:   stall draw = word (t % 4) of Philox(node, q, t / 4, instance ^ 2^31);
 //           stalled: I = Iprev, else I = I0 * D; Iprev <- I.
 //   TApSA:  ring[q % window] <- D; I = I0 * (sum of the ring) / window.
-//   x:      NORTHSTAR lambda I + I0 delta, LISTING lambda (I + I0 delta),
+//   x:      SCALED lambda I + I0 delta, LISTING lambda (I + I0 delta),
 //           EQUATION lambda (I + delta).
 __device__ __forceinline__ float variant_x(int mode, float I0, float lam, float del, float I) {
     if (mode == 1) return __fmul_rn(lam, __fmaf_rn(I0, del, I));

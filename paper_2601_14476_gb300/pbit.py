@@ -28,7 +28,7 @@ PBIT_E_NOTFOUND = -7
 
 PBIT_GRAPH_DENSE = 1
 
-OFFSET_NORTHSTAR, OFFSET_LISTING, OFFSET_EQUATION = 0, 1, 2
+OFFSET_SCALED, OFFSET_LISTING, OFFSET_EQUATION = 0, 1, 2
 KERNEL_AUTO, KERNEL_SPARSE, KERNEL_DENSE, KERNEL_RESIDENT = 0, 1, 2, 3
 ALG_PSA, ALG_SPSA, ALG_TAPSA = 0, 1, 2
 
@@ -227,7 +227,7 @@ def pbit_mean_s(n, src, dst, w) -> float:
 
 
 def make_params(trials, steps, step_begin=0, step_end=0, i0_min=0.1, i0_max=10.0, i0_normalize=1,
-                offset_mode=OFFSET_NORTHSTAR, seed=1, instance=0, kernel=KERNEL_AUTO, variability=None,
+                offset_mode=OFFSET_SCALED, seed=1, instance=0, kernel=KERNEL_AUTO, variability=None,
                 stream=None, algorithm=ALG_PSA, stall_prob=0.5, window=4, t_res=0, nu_dev=None, state=None):
     """Build a pbit_anneal_params; returns (params, keepalive) - keep both alive during the call."""
     p = pbit_anneal_params()

@@ -96,7 +96,7 @@ def test_dense_anneal_equals_sparse_anneal(n, T):
     G.status()
 
 
-@pytest.mark.parametrize("mode", [pbit.OFFSET_NORTHSTAR, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+@pytest.mark.parametrize("mode", [pbit.OFFSET_SCALED, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
 def test_dense_lockstep_vs_oracle(mode):
     n, T, S = 400, 64, 40
     g = _complete(n, 11)

@@ -73,7 +73,7 @@ def test_schedule_bit_exact():
     assert G.info()["mean_s"] == oracle.mean_s(csr)
 
 
-def _lockstep(g, T, steps, var, kernel, seed=11, instance=3, mode=pbit.OFFSET_NORTHSTAR, c=(0.1, 10.0), S=None):
+def _lockstep(g, T, steps, var, kernel, seed=11, instance=3, mode=pbit.OFFSET_SCALED, c=(0.1, 10.0), S=None):
     """Advance one step at a time on the GPU; check each step against the oracle from the GPU's state."""
     G = pbit.Graph.from_inputs(g)
     csr = oracle.Csr(g.n, g.src, g.dst, g.w)
@@ -101,7 +101,7 @@ def _lockstep(g, T, steps, var, kernel, seed=11, instance=3, mode=pbit.OFFSET_NO
 
 
 @pytest.mark.parametrize("kernel", [pbit.KERNEL_SPARSE, pbit.KERNEL_RESIDENT])
-@pytest.mark.parametrize("mode", [pbit.OFFSET_NORTHSTAR, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+@pytest.mark.parametrize("mode", [pbit.OFFSET_SCALED, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
 def test_lockstep_decisions(kernel, mode):
     g = inputs.erdos_renyi_gnm(400, 3000, 2, "pm1")
     var = inputs.variability(g.n, 2, s_intensity=0.3, s_offset=0.3)

@@ -23,7 +23,7 @@ def _host(t):
     return t.cpu().numpy()
 
 
-def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mode=pbit.OFFSET_NORTHSTAR):
+def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mode=pbit.OFFSET_SCALED):
     g = inputs.erdos_renyi_gnm(500, 2500, 3, "pm1")
     var = inputs.variability(g.n, 3, s_intensity=0.3, s_offset=0.3)
     G = pbit.Graph.from_inputs(g)
@@ -64,7 +64,7 @@ def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mo
     return mismatches
 
 
-@pytest.mark.parametrize("mode", [pbit.OFFSET_NORTHSTAR, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+@pytest.mark.parametrize("mode", [pbit.OFFSET_SCALED, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
 def test_spsa_lockstep(mode):
     assert _lockstep(pbit.ALG_SPSA, mode=mode) <= 2
 

@@ -246,7 +246,7 @@ def test_pbit_probability_is_one_plus_tanh_over_two():
 
 
 def test_offset_modes_recover_x():
-    """x from (gap + r): North-star I0(l D + d), listing l I0 (D + d), equation l (I0 D + d)."""
+    """x from (gap + r): scaled I0(l D + d), listing l I0 (D + d), equation l (I0 D + d)."""
     n, src, dst, w = _star(5, w=-1)
     csr = oracle.Csr(n, src, dst, w)
     T = 8
@@ -257,7 +257,7 @@ def test_offset_modes_recover_x():
     var = {"intensity": np.full(n, lam, np.float32), "offset": np.full(n, dl, np.float32)}
     I0 = np.float32(0.11)
     lam64, dl64, I064 = float(lam), float(dl), float(I0)
-    want = {oracle.OFFSET_NORTHSTAR: I064 * (lam64 * 3 + dl64),
+    want = {oracle.OFFSET_SCALED: I064 * (lam64 * 3 + dl64),
             oracle.OFFSET_LISTING: lam64 * I064 * (3 + dl64),
             oracle.OFFSET_EQUATION: lam64 * (I064 * 3 + dl64)}
     for mode, x in want.items():

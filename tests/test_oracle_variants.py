@@ -27,7 +27,7 @@ def test_spsa_without_stalls_is_psa():
         assert np.array_equal(a, b), q
 
 
-@pytest.mark.parametrize("mode", [oracle.OFFSET_NORTHSTAR, oracle.OFFSET_LISTING, oracle.OFFSET_EQUATION])
+@pytest.mark.parametrize("mode", [oracle.OFFSET_SCALED, oracle.OFFSET_LISTING, oracle.OFFSET_EQUATION])
 def test_tapsa_window_one_is_psa(mode):
     g, csr, s, var = _setup()
     tab = oracle.schedule(csr, 0.1, 10.0, 10)
