@@ -93,3 +93,18 @@ def test_generators_shapes():
     assert np.all((v["p_update"] >= 0) & (v["p_update"] <= 1)) and abs(v["p_update"].mean() - 0.9) < 0.01
     b = inputs.batch64(1, count=8, steps=10)
     assert [w.trials for w in b] == [32, 64, 128, 256, 32, 64, 128, 256]
+
+
+def test_sweep_grid_points_draw_the_stated_spreads():
+    """Host side of the variability sweep: ideal points carry no arrays; others draw Eq. 7's spreads."""
+    import numpy as np
+
+    from paper_2601_14476_gb300 import sweep
+
+    assert sweep.point_variability(100, 1, sweep.SweepPoint()) is None
+    v = sweep.point_variability(40000, 2, sweep.SweepPoint(s_intensity=0.2, s_offset=0.05, p_mean=0.8, s_p=0.1))
+    assert abs(v["intensity"].mean() - 1.0) < 0.01 and abs(v["intensity"].std() - 0.2) < 0.01
+    assert abs(v["offset"].mean()) < 0.005 and abs(v["offset"].std() - 0.05) < 0.005
+    assert v["p_update"].min() >= 0.0 and v["p_update"].max() <= 1.0 and abs(v["p_update"].mean() - 0.8) < 0.01
+    grid = sweep.default_grid()
+    assert grid[0].ideal and len(set(grid)) == len(grid)
