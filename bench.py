@@ -55,15 +55,14 @@ def batch_traffic(tuning, steps: int):
     return per_chunk * (steps // chunk)
 
 
-def sparse_tile_kernel(g, T: int, steps: int) -> str:
-    """Name of the sparse kernel the library launches for this graph, trial count and step count.
-
-    Two or more plain-pSA steps run in one multi-step launch (unless PBIT_SPARSE_STEPWISE is set).
+def sparse_tile_kernel(g, T: int, launches_per_anneal: float, steps: int) -> str:
+    """Name of the sparse kernel the library launched: the multi-step kernel when an anneal took far
+    fewer launches than steps, else the one-step kernel of the graph's tile form.
 
     Same rule as the library's tile choice: the warp-table tile needs unit weights and
     2 * max degree + 1 lanes per node segment of min(32, T / G) lanes (G = 32 or 16).
     """
-    if steps >= 2 and not os.environ.get("PBIT_SPARSE_STEPWISE"):
+    if steps >= 2 and launches_per_anneal < steps / 2:
         return "sparse_flow_kernel"
     deg = int(np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).max()) if g.m else 0
     if np.all(np.abs(g.w) == 1) and deg <= 15:
@@ -554,6 +553,7 @@ def main():
     torch.cuda.synchronize()
     G.status()
     anneal_ms = ka.elapsed_time(kb)
+    anneal_launches = pbit.pbit_launch_count() - l0
     pk = peaks()
     if chosen == pbit.KERNEL_DENSE:
         # 2 n^2 T flops per step (algorithmic, unpadded), e4m3 tensor peak = 2 x the measured bf16 peak
@@ -567,7 +567,7 @@ def main():
                     "peak_source": f"{pk['source']} bf16 sustained x2 (e4m3 nominal ratio)",
                     "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
     else:
-        kname = sparse_tile_kernel(g, T, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
+        kname = sparse_tile_kernel(g, T, anneal_launches, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
         launches_main = S if kname in ("sparse_warp_kernel", "sparse_step_kernel") else 1
         per_launch_ms = anneal_ms / launches_main
         mean_deg = 2.0 * g.m / g.n

@@ -148,7 +148,7 @@ static pbit_status select_kernel(const Graph& g, int requested, int32_t T, int* 
         if (dense_shape_ok(g, T, nullptr))
             k = PBIT_KERNEL_DENSE;
         else
-            k = resident_fits(g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
+            k = resident_preferred(g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
     }
     *out = k;
     return PBIT_OK;
@@ -557,26 +557,33 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     const SparseVariant variant = choose_sparse_variant(*g, T);
     // plain pSA over two or more steps: one persistent launch with per-tile step dependencies
     static const bool stepwise = std::getenv("PBIT_SPARSE_STEPWISE") != nullptr;  // force one launch per step
+    // PBIT_SPARSE_FLOW=always takes the multi-step form whatever the dependency structure (tests)
+    static const char* flow_env = std::getenv("PBIT_SPARSE_FLOW");
+    static const bool flow_forced = flow_env && std::string(flow_env) == "always";
     if (!stepwise && k >= 2 && !is_variant(a)) {
         int8_t* P = ((k - 1) % 2 == 0) ? spins_out : scratch;  // written at even j
         int8_t* Q = P == spins_out ? scratch : spins_out;
+        bool use_flow;
         {
             std::lock_guard<std::mutex> lock(g->mu);
             if ((st = ensure_flow_deps(*g, T, cur, P, Q, variant)) != PBIT_OK) return st;
+            use_flow = flow_forced || g->flow.local();
         }
-        unsigned* tile_done = nullptr;
-        unsigned* step_done = nullptr;
-        unsigned long long* next = nullptr;
-        if ((st = cb.alloc(&tile_done, (size_t)g->flow.ntiles)) != PBIT_OK) return st;
-        if ((st = cb.alloc(&step_done, (size_t)k)) != PBIT_OK) return st;
-        if ((st = cb.alloc(&next, 1)) != PBIT_OK) return st;
-        PBIT_CUDA_TRY(cudaMemsetAsync(tile_done, 0, sizeof(unsigned) * g->flow.ntiles, s));
-        PBIT_CUDA_TRY(cudaMemsetAsync(step_done, 0, sizeof(unsigned) * (size_t)k, s));
-        PBIT_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
-        a.step = b;
-        const cudaError_t fe = launch_sparse_flow(*g, a, k, cur, P, Q, tile_done, step_done, next, variant, s);
-        if (fe == cudaSuccess) return PBIT_OK;
-        if (fe != cudaErrorNotSupported) return cuda_fail(fe, "sparse multi-step launch");
+        if (use_flow) {
+            unsigned* tile_done = nullptr;
+            unsigned* step_done = nullptr;
+            unsigned long long* next = nullptr;
+            if ((st = cb.alloc(&tile_done, (size_t)g->flow.ntiles)) != PBIT_OK) return st;
+            if ((st = cb.alloc(&step_done, (size_t)k)) != PBIT_OK) return st;
+            if ((st = cb.alloc(&next, 1)) != PBIT_OK) return st;
+            PBIT_CUDA_TRY(cudaMemsetAsync(tile_done, 0, sizeof(unsigned) * g->flow.ntiles, s));
+            PBIT_CUDA_TRY(cudaMemsetAsync(step_done, 0, sizeof(unsigned) * (size_t)k, s));
+            PBIT_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned long long), s));
+            a.step = b;
+            const cudaError_t fe = launch_sparse_flow(*g, a, k, cur, P, Q, tile_done, step_done, next, variant, s);
+            if (fe == cudaSuccess) return PBIT_OK;
+            if (fe != cudaErrorNotSupported) return cuda_fail(fe, "sparse multi-step launch");
+        }
     }
     for (int32_t j = 0; j < k; ++j) {
         int8_t* dst = ((k - 1 - j) % 2 == 0) ? spins_out : scratch;

@@ -45,6 +45,12 @@ struct FlowDeps {
     int32_t* ptr = nullptr;  // device [ntiles + 1]
     int32_t* idx = nullptr;  // device
     int64_t listed = 0;      // tiles with their own list (the rest wait for the whole step)
+    int64_t entries = 0;     // total length of those lists
+    // Worth one persistent launch only when the dependencies are local: nearly every tile has a short
+    // list and there are enough tiles for steps to overlap.  Measured on GB300 (µs per step, multi-step
+    // vs one launch per step): 100x200 torus T=1024 34.9 vs 36.2; random graphs (G(n, 3n), 3-NN points
+    // numbered at random) 1.1-2x slower, their tiles all waiting on one step counter.
+    bool local() const { return ntiles >= 64 && listed * 10 >= (int64_t)ntiles * 9 && entries <= 16 * listed; }
 };
 
 struct Graph {
@@ -168,6 +174,10 @@ cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t*
 cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_ns, int* err, cudaStream_t s);
 // resident single-CTA anneal: all steps in one launch, spins in shared memory
 bool resident_fits(const Graph& g, int32_t T);
+// AUTO picks the single-CTA resident kernel only for small steps: one SM gathers about 2e10
+// neighbour-updates per second, and a multi-SM step costs about 12 µs (measured on GB300: G(800, 19176),
+// T = 16 runs 31 µs per step resident and 13 µs sparse), so the break-even is about 2.4e5 gathers.
+bool resident_preferred(const Graph& g, int32_t T);
 cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,
                                    cudaStream_t s);
 

@@ -488,6 +488,7 @@ static pbit_status build_flow_deps(Graph& g, int32_t groups) {
     if (ntiles >= (int64_t(1) << 31)) return fail(PBIT_E_INVALID, "flow: too many tiles");
     std::vector<int32_t> ptr((size_t)ntiles + 1, 0), idx, d;
     int64_t listed = 0;
+    g.flow.entries = 0;
     for (int64_t t = 0; t < ntiles; ++t) {
         const int64_t first = t * kBlock, last = std::min(items, first + kBlock) - 1;
         d.clear();
@@ -512,6 +513,7 @@ static pbit_status build_flow_deps(Graph& g, int32_t groups) {
         if (!global) {
             idx.insert(idx.end(), d.begin(), d.end());
             ++listed;
+            g.flow.entries += (int64_t)d.size();
         }
         ptr[(size_t)t + 1] = (int32_t)idx.size();
     }
@@ -526,9 +528,11 @@ static pbit_status build_flow_deps(Graph& g, int32_t groups) {
         g.flow = FlowDeps();
         return cuda_fail(e, "flow dependency lists");
     }
+    const int64_t entries = g.flow.entries;
     g.flow.groups = groups;
     g.flow.ntiles = (int32_t)ntiles;
     g.flow.listed = listed;
+    g.flow.entries = entries;
     return PBIT_OK;
 }
 
@@ -581,6 +585,10 @@ cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_
     bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(flag, budget_ns, err);
     count_launches(1);
     return cudaGetLastError();
+}
+
+bool resident_preferred(const Graph& g, int32_t T) {
+    return resident_fits(g, T) && (double)T * ((double)g.nnz + (double)g.n) <= 2.4e5;
 }
 
 bool resident_fits(const Graph& g, int32_t T) {

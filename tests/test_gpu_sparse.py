@@ -341,7 +341,9 @@ def test_warp_tile_equals_block_tile(tmp_path):
 def test_multistep_flow_equals_stepwise(tmp_path):
     """One persistent multi-step launch gives exactly the spins of one launch per step (forced in a child).
 
-    Covers the warp-table and block-table tiles, tile dependency lists and whole-step waits (random
+    The multi-step form is forced for every graph (by default only graphs with local tile dependencies
+    take it) and compared with forced per-step launches and with the default.  Covers the warp-table and
+    block-table tiles, tile dependency lists and whole-step waits (random
     graph), nodes spanning two tiles (T = 16384), and in-place resumes with odd and even step counts.
     """
     import os
@@ -369,7 +371,7 @@ def test_multistep_flow_equals_stepwise(tmp_path):
         "print('launches', pbit.pbit_launch_count())\n"
         "np.savez(%r, *outs)\n")
     res, launches = [], []
-    for k, extra in enumerate(({}, {"PBIT_SPARSE_STEPWISE": "1"})):
+    for k, extra in enumerate(({"PBIT_SPARSE_FLOW": "always"}, {"PBIT_SPARSE_STEPWISE": "1"}, {})):
         path = str(tmp_path / f"f{k}.npz")
         r = subprocess.run([sys.executable, "-c", code % path], check=True, env=dict(os.environ, **extra),
                            timeout=300, capture_output=True, text=True)
@@ -377,7 +379,9 @@ def test_multistep_flow_equals_stepwise(tmp_path):
         res.append(np.load(path))
     for key in res[0].files:
         assert np.array_equal(res[0][key], res[1][key]), key
+        assert np.array_equal(res[2][key], res[1][key]), key
     assert launches[0] < launches[1] // 10, launches
+    assert launches[2] < launches[1], launches  # the default takes the multi-step form for the tori
 
 
 def test_torus_full_run_mean_cut_matches_oracle():
