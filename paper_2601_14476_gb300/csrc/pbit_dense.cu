@@ -35,6 +35,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -384,6 +385,7 @@ struct PersistArgs {
     uint8_t* buf1;
     int32_t step_begin, step_end;
     unsigned* done;   // [RB * TB], zero on entry
+    int32_t tb_base;  // first trial block of this launch (launches cover consecutive groups)
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
     __shared__ int s_abort;
 
     cg::cluster_group cluster = cg::this_cluster();
-    const int ks = blockIdx.x, rb = blockIdx.y, tb = blockIdx.z;
+    const int ks = blockIdx.x, rb = blockIdx.y, tb = blockIdx.z + pa.tb_base;
     const int RB = gridDim.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool control = warp == kEpi / 32;
@@ -843,10 +845,19 @@ cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t*
     int max_clusters = 0;
     ce = cudaOccupancyMaxActiveClusters(&max_clusters, dense_persistent_kernel, &cfg);
     if (ce != cudaSuccess) return ce;
-    if (max_clusters < RB * TB) return cudaErrorNotSupported;
-    ce = cudaLaunchKernelEx(&cfg, dense_persistent_kernel, pa);
-    count_launches(1);
-    return ce;
+    // Every CTA of one launch must be resident at once (they wait on one another's flags).  Trial
+    // blocks never interact, so when they do not all fit, consecutive groups of trial blocks run as
+    // separate launches over the whole step range, each on its own trial columns and flags.
+    const int per_launch = std::min(TB, max_clusters / RB);
+    if (per_launch < 1) return cudaErrorNotSupported;
+    for (int g0 = 0; g0 < TB; g0 += per_launch) {
+        pa.tb_base = g0;
+        cfg.gridDim.z = (unsigned)std::min(per_launch, TB - g0);
+        ce = cudaLaunchKernelEx(&cfg, dense_persistent_kernel, pa);
+        count_launches(1);
+        if (ce != cudaSuccess) return ce;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_dense_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,

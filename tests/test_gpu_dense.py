@@ -146,19 +146,23 @@ def test_dense_full_size_sampled():
     G.status()
 
 
-def test_dense_persistent_equals_stepwise(tmp_path):
-    """The persistent tensor-core kernel equals one launch per step (forced in a child process)."""
+@pytest.mark.parametrize("n,T", [(700, 128), (2000, 384)])
+def test_dense_persistent_equals_stepwise(tmp_path, n, T):
+    """The persistent tensor-core kernel equals one launch per step (forced in a child process).
+
+    n = 2000, T = 384: three trial blocks of 64 CTAs do not fit at once, so they run as two
+    persistent launches (two blocks, then one)."""
     import os
     import subprocess
     import sys
     code = (
         "import numpy as np, torch\n"
         "from paper_2601_14476_gb300 import inputs, pbit\n"
-        "g = inputs.complete_pm1(700, 5)\n"
-        "var = inputs.variability(700, 5)\n"
+        f"g = inputs.complete_pm1({n}, 5)\n"
+        f"var = inputs.variability({n}, 5)\n"
         "G = pbit.Graph.from_inputs(g, dense=True)\n"
         "l0 = pbit.pbit_launch_count()\n"
-        "out = G.anneal(128, 77, seed=4, variability=var, kernel=pbit.KERNEL_DENSE)\n"
+        f"out = G.anneal({T}, 77, seed=4, variability=var, kernel=pbit.KERNEL_DENSE)\n"
         "torch.cuda.synchronize(); G.status()\n"
         "launches = pbit.pbit_launch_count() - l0\n"
         "import os\n"
