@@ -34,8 +34,8 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of each dominant kernel from one ncu capture (profiles/*.md), valid only while
 # the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
 TRAFFIC = {
-    "dense_persistent_kernel": {"bytes": 4896256 + 176896, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "bb6c802c447f213d",
+    "dense_persistent_kernel": {"bytes": 5209088 + 251392, "files": ["pbit_dense.cu", "pbit_device.cuh"],
+                                "sha": "64bcd12d262e1219",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
     "sparse_flow_kernel": {"bytes": 23933952 + 166513920,
                            "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
