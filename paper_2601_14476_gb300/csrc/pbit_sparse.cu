@@ -154,7 +154,7 @@ __device__ __forceinline__ void flow_red_release_add(unsigned* p, unsigned v) {
 }
 
 template <int G, bool WARP, bool UNIT, bool TABLE>
-__global__ void __launch_bounds__(kBlock, WARP ? (6) : 1) sparse_flow_kernel(FlowArgs f) {
+__global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowArgs f) {
     __shared__ uint32_t s_tab[TABLE ? kTabMax : 1];
     __shared__ unsigned long long s_item;
     __shared__ int s_ok;
