@@ -36,24 +36,6 @@ pbit_status cuda_fail(cudaError_t err, const char* what) {
 }
 
 // --------------------------------------------------------------- schedule ---
-// mean_i sqrt((n-1) Var(J_i,:)) with the population variance over the full
-// row of length n (zeros included), summed in node order in FP64.
-static double compute_mean_s(int32_t n, const std::vector<int32_t>& row_ptr, const std::vector<int8_t>& J) {
-    double acc = 0.0;
-    for (int32_t i = 0; i < n; ++i) {
-        int64_t s1 = 0, s2 = 0;
-        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            s1 += J[k];
-            s2 += (int64_t)J[k] * J[k];
-        }
-        const double mean = (double)s1 / (double)n;
-        double var = (double)s2 / (double)n - mean * mean;
-        if (var < 0.0) var = 0.0;
-        acc += std::sqrt((double)(n - 1) * var);
-    }
-    return acc / (double)n;
-}
-
 pbit_status build_schedule(const Graph& g, double i0_min, double i0_max, int normalize, int steps,
                            std::vector<float>& out) {
     if (steps < 1) return fail(PBIT_E_INVALID, "schedule: steps must be >= 1");
@@ -169,81 +151,110 @@ static pbit_status build_host(Graph& g, int32_t n, int64_t n_edges, const int32_
     if (n_edges < 0 || n_edges > (int64_t)0x3FFFFFFF) return fail(PBIT_E_INVALID, "graph: bad edge count");
     if (n_edges > 0 && (!src || !dst || !w)) return fail(PBIT_E_INVALID, "graph: NULL edge arrays");
     if (n_edges > (int64_t)n * (n - 1) / 2) return fail(PBIT_E_INVALID, "graph: more edges than node pairs");
+    // validation; `canonical`: edges strictly increasing in (src, dst) with src < dst
+    bool canonical = true;
+    std::vector<int32_t> deg((size_t)n + 1, 0);
+    int64_t wsum = 0;
+    g.unit_weights = true;
     for (int64_t e = 0; e < n_edges; ++e) {
-        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || a >= n || b < 0 || b >= n)
             return fail(PBIT_E_INVALID, "graph: edge endpoint out of range at " + std::to_string(e));
-        if (src[e] == dst[e]) return fail(PBIT_E_INVALID, "graph: self loop at " + std::to_string(e));
+        if (a == b) return fail(PBIT_E_INVALID, "graph: self loop at " + std::to_string(e));
         if (w[e] == -128) return fail(PBIT_E_INVALID, "graph: weight -128 (J = -w overflows int8)");
+        canonical = canonical && a < b && (e == 0 || a > src[e - 1] || (a == src[e - 1] && b > dst[e - 1]));
+        deg[(size_t)a + 1]++;
+        deg[(size_t)b + 1]++;
+        wsum += w[e];
+        if (w[e] != 1 && w[e] != -1) g.unit_weights = false;
     }
     g.n = n;
     g.n_edges = n_edges;
     g.nnz = 2 * n_edges;
-    std::vector<int32_t> deg((size_t)n + 1, 0);
-    for (int64_t e = 0; e < n_edges; ++e) {
-        deg[(size_t)src[e] + 1]++;
-        deg[(size_t)dst[e] + 1]++;
-    }
+    g.total_weight = wsum;
     g.h_row_ptr.assign((size_t)n + 1, 0);
     for (int32_t i = 0; i < n; ++i) g.h_row_ptr[(size_t)i + 1] = g.h_row_ptr[(size_t)i] + deg[(size_t)i + 1];
     g.h_col.resize((size_t)std::max<int64_t>(g.nnz, 1));
     g.h_J.resize((size_t)std::max<int64_t>(g.nnz, 1));
     std::vector<int32_t> fill(g.h_row_ptr.begin(), g.h_row_ptr.end() - 1);
-    int64_t wsum = 0;
-    g.unit_weights = true;
-    for (int64_t e = 0; e < n_edges; ++e) {
-        const int8_t J = (int8_t)(-w[e]);
-        g.h_col[(size_t)fill[(size_t)src[e]]] = dst[e];
-        g.h_J[(size_t)fill[(size_t)src[e]]++] = J;
-        g.h_col[(size_t)fill[(size_t)dst[e]]] = src[e];
-        g.h_J[(size_t)fill[(size_t)dst[e]]++] = J;
-        wsum += w[e];
-        if (w[e] != 1 && w[e] != -1) g.unit_weights = false;
+    if (canonical) {
+        // one pass: row r first receives the edges (s, r), s < r, in increasing s, then the edges
+        // (r, d), r < d, in increasing d, so every row comes out sorted by column
+        for (int64_t e = 0; e < n_edges; ++e) {
+            const int8_t J = (int8_t)(-w[e]);
+            const int32_t a = src[e], b = dst[e];
+            g.h_col[(size_t)fill[(size_t)a]] = b;
+            g.h_J[(size_t)fill[(size_t)a]++] = J;
+            g.h_col[(size_t)fill[(size_t)b]] = a;
+            g.h_J[(size_t)fill[(size_t)b]++] = J;
+        }
+    } else {
+        // any order: two stable counting passes over the 2m directed entries, first bucketed by
+        // column (the column pointer equals the row pointer), then, visiting columns in order, by row
+        std::vector<int32_t> by_col_row((size_t)std::max<int64_t>(g.nnz, 1));
+        std::vector<int8_t> by_col_J((size_t)std::max<int64_t>(g.nnz, 1));
+        for (int64_t e = 0; e < n_edges; ++e) {
+            const int8_t J = (int8_t)(-w[e]);
+            const int32_t a = src[e], b = dst[e];
+            by_col_row[(size_t)fill[(size_t)b]] = a;  // entry (a, b) lands in column b
+            by_col_J[(size_t)fill[(size_t)b]++] = J;
+            by_col_row[(size_t)fill[(size_t)a]] = b;  // entry (b, a) lands in column a
+            by_col_J[(size_t)fill[(size_t)a]++] = J;
+        }
+        std::copy(g.h_row_ptr.begin(), g.h_row_ptr.end() - 1, fill.begin());
+        for (int32_t c = 0; c < n; ++c) {
+            for (int32_t k = g.h_row_ptr[(size_t)c]; k < g.h_row_ptr[(size_t)c + 1]; ++k) {
+                const int32_t r = by_col_row[(size_t)k];
+                g.h_col[(size_t)fill[(size_t)r]] = c;
+                g.h_J[(size_t)fill[(size_t)r]++] = by_col_J[(size_t)k];
+            }
+        }
     }
-    g.total_weight = wsum;
-    std::vector<std::pair<int32_t, int8_t>> row;
+    // per row: duplicate check, W_i = sum_j |J_ij|, the field bound, and the sums of mean(s_i)
     int64_t max_field = 0;
     g.max_degree = 0;
-    for (int32_t i = 0; i < n; ++i) {
-        const int32_t b = g.h_row_ptr[(size_t)i], e = g.h_row_ptr[(size_t)i + 1];
-        g.max_degree = std::max(g.max_degree, e - b);
-        row.clear();
-        int64_t absum = 0;
-        for (int32_t k = b; k < e; ++k) {
-            row.emplace_back(g.h_col[(size_t)k], g.h_J[(size_t)k]);
-            absum += std::abs((int32_t)g.h_J[(size_t)k]);
-        }
-        std::sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-        for (size_t k = 1; k < row.size(); ++k)
-            if (row[k].first == row[k - 1].first)
-                return fail(PBIT_E_INVALID, "graph: duplicate edge (" + std::to_string(i) + "," +
-                                                std::to_string(row[k].first) + ")");
-        for (int32_t k = b; k < e; ++k) {
-            g.h_col[(size_t)k] = row[(size_t)(k - b)].first;
-            g.h_J[(size_t)k] = row[(size_t)(k - b)].second;
-        }
-        const int64_t hi = h ? std::llabs((long long)h[i]) : 0;
-        max_field = std::max(max_field, absum + hi);
-    }
-    if (max_field >= (1 << 24)) return fail(PBIT_E_INVALID, "graph: |field| could reach 2^24");
-    // per-node field half-width W_i and threshold-table offsets
     g.h_wabs.assign((size_t)n, 0);
     g.h_tab_off.assign((size_t)n + 1, 0);
     int64_t acc_off = 0;
     g.max_wabs = 0;
+    double s_acc = 0.0;
+    int32_t max_abs_J = 0;
     for (int32_t i = 0; i < n; ++i) {
-        int32_t W = 0;
-        for (int32_t k = g.h_row_ptr[(size_t)i]; k < g.h_row_ptr[(size_t)i + 1]; ++k) W += std::abs((int32_t)g.h_J[(size_t)k]);
+        const int32_t b = g.h_row_ptr[(size_t)i], e = g.h_row_ptr[(size_t)i + 1];
+        g.max_degree = std::max(g.max_degree, e - b);
+        int64_t absum = 0, s1 = 0, s2 = 0;
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t J = g.h_J[(size_t)k];
+            const int32_t aJ = J < 0 ? -J : J;
+            absum += aJ;
+            max_abs_J = std::max(max_abs_J, aJ);
+            s1 += J;
+            s2 += (int64_t)J * J;
+            if (!canonical && k > b && g.h_col[(size_t)k] == g.h_col[(size_t)k - 1])
+                return fail(PBIT_E_INVALID, "graph: duplicate edge (" + std::to_string(i) + "," +
+                                                std::to_string(g.h_col[(size_t)k]) + ")");
+        }
+        const int64_t hi = h ? std::llabs((long long)h[i]) : 0;
+        max_field = std::max(max_field, absum + hi);
+        const int32_t W = (int32_t)std::min<int64_t>(absum, INT32_MAX);
         g.h_wabs[(size_t)i] = W;
         g.max_wabs = std::max(g.max_wabs, W);
         g.h_tab_off[(size_t)i] = (int32_t)std::min<int64_t>(acc_off, INT32_MAX);
         acc_off += (int64_t)W + 1;
+        // s_i = sqrt((n - 1) Var(J_i,:)), population variance over the full row of n entries
+        const double mean = (double)s1 / (double)n;
+        double var = (double)s2 / (double)n - mean * mean;
+        if (var < 0.0) var = 0.0;
+        s_acc += std::sqrt((double)(n - 1) * var);
     }
+    g.mean_s = s_acc / (double)n;
+    g.max_abs_J = max_abs_J;
+    if (max_field >= (1 << 24)) return fail(PBIT_E_INVALID, "graph: |field| could reach 2^24");
     g.tab_ok = acc_off < INT32_MAX;
     g.h_tab_off[(size_t)n] = (int32_t)std::min<int64_t>(acc_off, INT32_MAX);
     g.max_abs_field = (int32_t)max_field;
     g.has_h = h != nullptr;
     if (h) g.h_h.assign(h, h + n);
-    g.mean_s = compute_mean_s(n, g.h_row_ptr, g.h_J);
     return PBIT_OK;
 }
 

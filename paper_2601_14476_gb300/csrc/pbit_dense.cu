@@ -683,7 +683,7 @@ size_t dense_smem_bytes(int NT) {
     return 128 + (size_t)kRows * kSlice + (size_t)NT * kSlice + (size_t)kRows * (NT + kPad) * sizeof(float) + 64;
 }
 
-uint8_t e4m3_of_int(int v) {
+__host__ __device__ uint8_t e4m3_of_int(int v) {
     // exact e4m3 encoding of an integer with |v| <= 16
     if (v == 0) return 0;
     const uint8_t sign = v < 0 ? 0x80 : 0;
@@ -709,32 +709,39 @@ bool dense_shape_ok(const Graph& g, int32_t T, std::string* why) {
     return true;
 }
 
+// One block per row of J: scatter the row's CSR entries, as e4m3 bytes, into the MMA tile order
+// (the zero-filled buffer holds e4m3 zeros elsewhere).
+__global__ void dense_operand_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                     const int8_t* __restrict__ J, int32_t KS, uint8_t* __restrict__ tiles) {
+    const int i = blockIdx.x;
+    const int rb = i / kRows, rg = (i % kRows) >> 3, rr = i & 7;
+    const size_t row_base = (size_t)rb * KS * (size_t)(kRows * kSlice) + (size_t)rg * (kCores * 128) + (size_t)rr * 16;
+    for (int k = row_ptr[i] + threadIdx.x; k < row_ptr[i + 1]; k += blockDim.x) {
+        const int j = col[k];
+        const int ks = j / kSlice, c = (j % kSlice) >> 4, b = j & 15;
+        tiles[row_base + (size_t)ks * (size_t)(kRows * kSlice) + (size_t)c * 128 + b] = e4m3_of_int(J[k]);
+    }
+}
+
 pbit_status build_dense_operand(Graph& g) {
     const int n_pad = ((g.n + kSlice - 1) / kSlice) * kSlice;
-    const int KS = n_pad / kSlice, RB = n_pad / kRows;
+    const int KS = n_pad / kSlice;
     if (KS > 16) return fail(PBIT_E_INVALID, "dense operand: n > 8192 is not supported by the tensor-core path");
-    for (size_t k = 0; k < g.h_J.size() && k < (size_t)g.nnz; ++k)
-        if (g.h_J[k] > 16 || g.h_J[k] < -16)
-            return fail(PBIT_E_INVALID, "dense operand: |w| > 16 is not exact in e4m3");
-    std::vector<uint8_t> tiles((size_t)n_pad * n_pad, 0);
-    for (int i = 0; i < g.n; ++i) {
-        const int rb = i / kRows, rg = (i % kRows) >> 3, rr = i & 7;
-        for (int k = g.h_row_ptr[(size_t)i]; k < g.h_row_ptr[(size_t)i + 1]; ++k) {
-            const int j = g.h_col[(size_t)k];
-            const int ks = j / kSlice, c = (j % kSlice) >> 4, b = j & 15;
-            const size_t off = ((size_t)rb * KS + ks) * (size_t)(kRows * kSlice) + (size_t)rg * (kCores * 128) +
-                               (size_t)c * 128 + (size_t)rr * 16 + b;
-            tiles[off] = e4m3_of_int(g.h_J[(size_t)k]);
-        }
-    }
-    (void)RB;
-    cudaError_t e = cudaMalloc((void**)&g.dense.J_e4m3, tiles.size());
+    if (g.max_abs_J > 16) return fail(PBIT_E_INVALID, "dense operand: |w| > 16 is not exact in e4m3");
+    const size_t bytes = (size_t)n_pad * n_pad;
+    cudaError_t e = cudaMalloc((void**)&g.dense.J_e4m3, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(dense J)");
-    e = cudaMemcpy(g.dense.J_e4m3, tiles.data(), tiles.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(dense J)");
+    e = cudaMemset(g.dense.J_e4m3, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(dense J)");
+    if (g.n > 0 && g.nnz > 0) {
+        dense_operand_kernel<<<(unsigned)g.n, 256>>>(g.row_ptr, g.col, g.J, KS, g.dense.J_e4m3);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "dense operand kernel");
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "dense operand kernel");
+    }
     g.dense.n_pad = n_pad;
-    g.dense.bytes = tiles.size();
-    g.device_bytes += tiles.size();
+    g.dense.bytes = bytes;
+    g.device_bytes += bytes;
     return PBIT_OK;
 }
 

@@ -64,6 +64,7 @@ struct Graph {
     double mean_s = 0.0;
     int64_t total_weight = 0;
     int32_t max_abs_field = 0;    // max_i |h_i| + sum_j |J_ij|
+    int32_t max_abs_J = 0;        // max |J_ij|
     // device arrays
     int32_t* row_ptr = nullptr;   // [n+1]
     int32_t* col = nullptr;       // [nnz]

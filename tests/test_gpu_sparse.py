@@ -402,3 +402,26 @@ def test_torus_full_run_mean_cut_matches_oracle():
     ref_cut = oracle.cut(g.src, g.dst, g.w, ref)
     assert np.array_equal(G.cut(_dev(out))[:K], gpu_cut)
     assert abs(gpu_cut.mean() - ref_cut.mean()) <= 0.005 * abs(ref_cut.mean()), (gpu_cut, ref_cut)
+
+
+def test_graph_from_any_edge_order_equals_canonical():
+    """The same graph given as a shuffled edge list with random orientations (the general CSR
+    build) gives the canonical build's fields, cut, schedule normalisation and anneal; a duplicate
+    edge in a shuffled list is rejected."""
+    g = inputs.rgg_knn(900, 8, 3, "pm1")
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(g.m)
+    flip = rng.integers(0, 2, g.m).astype(bool)
+    src = np.where(flip, g.dst, g.src)[perm].astype(np.int32)
+    dst = np.where(flip, g.src, g.dst)[perm].astype(np.int32)
+    w = g.w[perm]
+    A = pbit.Graph(g.n, g.src, g.dst, g.w)
+    B = pbit.Graph(g.n, src, dst, w)
+    assert A.info()["mean_s"] == B.info()["mean_s"]
+    s = _dev(inputs.random_spins(g.n, 32, 3))
+    assert np.array_equal(_host(A.fields(s)), _host(B.fields(s)))
+    assert np.array_equal(A.cut(s), B.cut(s))
+    var = inputs.variability(g.n, 3)
+    assert np.array_equal(_host(A.anneal(32, 40, seed=2, variability=var)), _host(B.anneal(32, 40, seed=2, variability=var)))
+    with pytest.raises(pbit.PbitError):
+        pbit.Graph(g.n, np.append(src, dst[5]), np.append(dst, src[5]), np.append(w, w[5]))
