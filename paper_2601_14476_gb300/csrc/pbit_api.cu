@@ -11,6 +11,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pbit_internal.h"
@@ -151,46 +152,108 @@ static pbit_status build_host(Graph& g, int32_t n, int64_t n_edges, const int32_
     if (n_edges < 0 || n_edges > (int64_t)0x3FFFFFFF) return fail(PBIT_E_INVALID, "graph: bad edge count");
     if (n_edges > 0 && (!src || !dst || !w)) return fail(PBIT_E_INVALID, "graph: NULL edge arrays");
     if (n_edges > (int64_t)n * (n - 1) / 2) return fail(PBIT_E_INVALID, "graph: more edges than node pairs");
-    // validation; `canonical`: edges strictly increasing in (src, dst) with src < dst
+    // P host threads for large graphs (at least 256K edges each; per-thread count arrays of n entries)
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    int P = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(hw, 16), n_edges >> 18));
+    while (P > 1 && (int64_t)P * n > (int64_t(4) << 20)) --P;
+    auto run = [P](auto&& f) {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < P; ++t) pool.emplace_back(f, t);
+        f(0);
+        for (auto& th : pool) th.join();
+    };
+    auto chunk = [&](int t) { return n_edges * t / P; };
+    // validation and per-thread endpoint counts; `canonical`: edges strictly increasing in
+    // (src, dst) with src < dst
+    struct Local {
+        int64_t wsum = 0, bad = -1;
+        bool unit = true, canonical = true;
+    };
+    std::vector<Local> loc((size_t)P);
+    std::vector<int32_t> cnt_src((size_t)P * n, 0), cnt_dst((size_t)P * n, 0);
+    run([&](int t) {
+        Local& L = loc[(size_t)t];
+        int32_t* cs = cnt_src.data() + (size_t)t * n;
+        int32_t* cd = cnt_dst.data() + (size_t)t * n;
+        for (int64_t e = chunk(t); e < chunk(t + 1); ++e) {
+            const int32_t a = src[e], b = dst[e];
+            if (a < 0 || a >= n || b < 0 || b >= n || a == b || w[e] == -128) {
+                L.bad = e;
+                return;
+            }
+            L.canonical = L.canonical && a < b && (e == 0 || a > src[e - 1] || (a == src[e - 1] && b > dst[e - 1]));
+            cs[a]++;
+            cd[b]++;
+            L.wsum += w[e];
+            if (w[e] != 1 && w[e] != -1) L.unit = false;
+        }
+    });
+    int64_t bad = -1;
+    for (const Local& L : loc)
+        if (L.bad >= 0 && (bad < 0 || L.bad < bad)) bad = L.bad;
+    if (bad >= 0) {
+        const int32_t a = src[bad], b = dst[bad];
+        if (a < 0 || a >= n || b < 0 || b >= n)
+            return fail(PBIT_E_INVALID, "graph: edge endpoint out of range at " + std::to_string(bad));
+        if (a == b) return fail(PBIT_E_INVALID, "graph: self loop at " + std::to_string(bad));
+        return fail(PBIT_E_INVALID, "graph: weight -128 (J = -w overflows int8)");
+    }
     bool canonical = true;
-    std::vector<int32_t> deg((size_t)n + 1, 0);
     int64_t wsum = 0;
     g.unit_weights = true;
-    for (int64_t e = 0; e < n_edges; ++e) {
-        const int32_t a = src[e], b = dst[e];
-        if (a < 0 || a >= n || b < 0 || b >= n)
-            return fail(PBIT_E_INVALID, "graph: edge endpoint out of range at " + std::to_string(e));
-        if (a == b) return fail(PBIT_E_INVALID, "graph: self loop at " + std::to_string(e));
-        if (w[e] == -128) return fail(PBIT_E_INVALID, "graph: weight -128 (J = -w overflows int8)");
-        canonical = canonical && a < b && (e == 0 || a > src[e - 1] || (a == src[e - 1] && b > dst[e - 1]));
-        deg[(size_t)a + 1]++;
-        deg[(size_t)b + 1]++;
-        wsum += w[e];
-        if (w[e] != 1 && w[e] != -1) g.unit_weights = false;
+    for (const Local& L : loc) {
+        canonical = canonical && L.canonical;
+        wsum += L.wsum;
+        g.unit_weights = g.unit_weights && L.unit;
     }
     g.n = n;
     g.n_edges = n_edges;
     g.nnz = 2 * n_edges;
     g.total_weight = wsum;
+    // out_deg / in_deg per node, and cnt_dst turned into each thread's first slot among the entries of
+    // every destination (exclusive prefix over the threads, which hold consecutive edge ranges)
+    std::vector<int32_t> out_deg((size_t)n), in_deg((size_t)n);
+    run([&](int t) {
+        for (int64_t v = (int64_t)n * t / P; v < (int64_t)n * (t + 1) / P; ++v) {
+            int32_t so = 0, si = 0;
+            for (int q = 0; q < P; ++q) {
+                so += cnt_src[(size_t)q * n + v];
+                const int32_t c = cnt_dst[(size_t)q * n + v];
+                cnt_dst[(size_t)q * n + v] = si;
+                si += c;
+            }
+            out_deg[(size_t)v] = so;
+            in_deg[(size_t)v] = si;
+        }
+    });
     g.h_row_ptr.assign((size_t)n + 1, 0);
-    for (int32_t i = 0; i < n; ++i) g.h_row_ptr[(size_t)i + 1] = g.h_row_ptr[(size_t)i] + deg[(size_t)i + 1];
+    for (int32_t i = 0; i < n; ++i) g.h_row_ptr[(size_t)i + 1] = g.h_row_ptr[(size_t)i] + out_deg[(size_t)i] + in_deg[(size_t)i];
     g.h_col.resize((size_t)std::max<int64_t>(g.nnz, 1));
     g.h_J.resize((size_t)std::max<int64_t>(g.nnz, 1));
-    std::vector<int32_t> fill(g.h_row_ptr.begin(), g.h_row_ptr.end() - 1);
     if (canonical) {
-        // one pass: row r first receives the edges (s, r), s < r, in increasing s, then the edges
-        // (r, d), r < d, in increasing d, so every row comes out sorted by column
-        for (int64_t e = 0; e < n_edges; ++e) {
-            const int8_t J = (int8_t)(-w[e]);
-            const int32_t a = src[e], b = dst[e];
-            g.h_col[(size_t)fill[(size_t)a]] = b;
-            g.h_J[(size_t)fill[(size_t)a]++] = J;
-            g.h_col[(size_t)fill[(size_t)b]] = a;
-            g.h_J[(size_t)fill[(size_t)b]++] = J;
-        }
+        // Row r holds first the edges (s, r), s < r, in increasing s (= edge order), then the edges
+        // (r, d) in increasing d, so it comes out sorted by column.  Edge e = (a, b) lands at
+        // row_ptr[a] + in_deg[a] + (e - first edge of a) and at row_ptr[b] + (its rank among the
+        // edges into b); the threads write disjoint slots.
+        std::vector<int64_t> first((size_t)n + 1, 0);
+        for (int32_t i = 0; i < n; ++i) first[(size_t)i + 1] = first[(size_t)i] + out_deg[(size_t)i];
+        run([&](int t) {
+            int32_t* rank = cnt_dst.data() + (size_t)t * n;
+            for (int64_t e = chunk(t); e < chunk(t + 1); ++e) {
+                const int8_t J = (int8_t)(-w[e]);
+                const int32_t a = src[e], b = dst[e];
+                const size_t up = (size_t)(g.h_row_ptr[(size_t)a] + in_deg[(size_t)a] + (e - first[(size_t)a]));
+                const size_t lo = (size_t)(g.h_row_ptr[(size_t)b] + rank[b]++);
+                g.h_col[up] = b;
+                g.h_J[up] = J;
+                g.h_col[lo] = a;
+                g.h_J[lo] = J;
+            }
+        });
     } else {
         // any order: two stable counting passes over the 2m directed entries, first bucketed by
         // column (the column pointer equals the row pointer), then, visiting columns in order, by row
+        std::vector<int32_t> fill(g.h_row_ptr.begin(), g.h_row_ptr.end() - 1);
         std::vector<int32_t> by_col_row((size_t)std::max<int64_t>(g.nnz, 1));
         std::vector<int8_t> by_col_J((size_t)std::max<int64_t>(g.nnz, 1));
         for (int64_t e = 0; e < n_edges; ++e) {
@@ -210,45 +273,69 @@ static pbit_status build_host(Graph& g, int32_t n, int64_t n_edges, const int32_
             }
         }
     }
-    // per row: duplicate check, W_i = sum_j |J_ij|, the field bound, and the sums of mean(s_i)
-    int64_t max_field = 0;
-    g.max_degree = 0;
+    // per row, in parallel over row ranges: duplicate check, W_i = sum_j |J_ij|, the field bound, and
+    // s_i = sqrt((n - 1) Var(J_i,:)) (population variance over the full row of n entries); mean(s_i)
+    // is then summed in node order
+    struct RowStats {
+        int64_t max_field = 0, dup_row = -1;
+        int32_t max_degree = 0, max_abs_J = 0, max_wabs = 0;
+    };
+    std::vector<RowStats> rs((size_t)P);
+    std::vector<double> s_row((size_t)n);
     g.h_wabs.assign((size_t)n, 0);
+    run([&](int t) {
+        RowStats& R = rs[(size_t)t];
+        for (int64_t i = (int64_t)n * t / P; i < (int64_t)n * (t + 1) / P; ++i) {
+            const int32_t b = g.h_row_ptr[(size_t)i], e = g.h_row_ptr[(size_t)i + 1];
+            R.max_degree = std::max(R.max_degree, e - b);
+            int64_t absum = 0, s1 = 0, s2 = 0;
+            for (int32_t k = b; k < e; ++k) {
+                const int32_t J = g.h_J[(size_t)k];
+                const int32_t aJ = J < 0 ? -J : J;
+                absum += aJ;
+                R.max_abs_J = std::max(R.max_abs_J, aJ);
+                s1 += J;
+                s2 += (int64_t)J * J;
+                if (!canonical && k > b && g.h_col[(size_t)k] == g.h_col[(size_t)k - 1] && R.dup_row < 0) R.dup_row = i;
+            }
+            const int64_t hi = h ? std::llabs((long long)h[i]) : 0;
+            R.max_field = std::max(R.max_field, absum + hi);
+            const int32_t W = (int32_t)std::min<int64_t>(absum, INT32_MAX);
+            g.h_wabs[(size_t)i] = W;
+            R.max_wabs = std::max(R.max_wabs, W);
+            const double mean = (double)s1 / (double)n;
+            double var = (double)s2 / (double)n - mean * mean;
+            if (var < 0.0) var = 0.0;
+            s_row[(size_t)i] = std::sqrt((double)(n - 1) * var);
+        }
+    });
+    int64_t max_field = 0, dup_row = -1;
+    g.max_degree = 0;
+    g.max_abs_J = 0;
+    g.max_wabs = 0;
+    for (const RowStats& R : rs) {
+        max_field = std::max(max_field, R.max_field);
+        g.max_degree = std::max(g.max_degree, R.max_degree);
+        g.max_abs_J = std::max(g.max_abs_J, R.max_abs_J);
+        g.max_wabs = std::max(g.max_wabs, R.max_wabs);
+        if (R.dup_row >= 0 && (dup_row < 0 || R.dup_row < dup_row)) dup_row = R.dup_row;
+    }
+    if (dup_row >= 0) {
+        const int32_t b = g.h_row_ptr[(size_t)dup_row], e = g.h_row_ptr[(size_t)dup_row + 1];
+        int32_t c = -1;
+        for (int32_t k = b + 1; k < e && c < 0; ++k)
+            if (g.h_col[(size_t)k] == g.h_col[(size_t)k - 1]) c = g.h_col[(size_t)k];
+        return fail(PBIT_E_INVALID, "graph: duplicate edge (" + std::to_string(dup_row) + "," + std::to_string(c) + ")");
+    }
     g.h_tab_off.assign((size_t)n + 1, 0);
     int64_t acc_off = 0;
-    g.max_wabs = 0;
     double s_acc = 0.0;
-    int32_t max_abs_J = 0;
     for (int32_t i = 0; i < n; ++i) {
-        const int32_t b = g.h_row_ptr[(size_t)i], e = g.h_row_ptr[(size_t)i + 1];
-        g.max_degree = std::max(g.max_degree, e - b);
-        int64_t absum = 0, s1 = 0, s2 = 0;
-        for (int32_t k = b; k < e; ++k) {
-            const int32_t J = g.h_J[(size_t)k];
-            const int32_t aJ = J < 0 ? -J : J;
-            absum += aJ;
-            max_abs_J = std::max(max_abs_J, aJ);
-            s1 += J;
-            s2 += (int64_t)J * J;
-            if (!canonical && k > b && g.h_col[(size_t)k] == g.h_col[(size_t)k - 1])
-                return fail(PBIT_E_INVALID, "graph: duplicate edge (" + std::to_string(i) + "," +
-                                                std::to_string(g.h_col[(size_t)k]) + ")");
-        }
-        const int64_t hi = h ? std::llabs((long long)h[i]) : 0;
-        max_field = std::max(max_field, absum + hi);
-        const int32_t W = (int32_t)std::min<int64_t>(absum, INT32_MAX);
-        g.h_wabs[(size_t)i] = W;
-        g.max_wabs = std::max(g.max_wabs, W);
         g.h_tab_off[(size_t)i] = (int32_t)std::min<int64_t>(acc_off, INT32_MAX);
-        acc_off += (int64_t)W + 1;
-        // s_i = sqrt((n - 1) Var(J_i,:)), population variance over the full row of n entries
-        const double mean = (double)s1 / (double)n;
-        double var = (double)s2 / (double)n - mean * mean;
-        if (var < 0.0) var = 0.0;
-        s_acc += std::sqrt((double)(n - 1) * var);
+        acc_off += (int64_t)g.h_wabs[(size_t)i] + 1;
+        s_acc += s_row[(size_t)i];
     }
     g.mean_s = s_acc / (double)n;
-    g.max_abs_J = max_abs_J;
     if (max_field >= (1 << 24)) return fail(PBIT_E_INVALID, "graph: |field| could reach 2^24");
     g.tab_ok = acc_off < INT32_MAX;
     g.h_tab_off[(size_t)n] = (int32_t)std::min<int64_t>(acc_off, INT32_MAX);

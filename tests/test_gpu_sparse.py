@@ -425,3 +425,26 @@ def test_graph_from_any_edge_order_equals_canonical():
     assert np.array_equal(_host(A.anneal(32, 40, seed=2, variability=var)), _host(B.anneal(32, 40, seed=2, variability=var)))
     with pytest.raises(pbit.PbitError):
         pbit.Graph(g.n, np.append(src, dst[5]), np.append(dst, src[5]), np.append(w, w[5]))
+
+
+def test_large_graph_build_threads_any_order():
+    """Graphs large enough for the threaded host build (over 512K edges): the canonical edge list and
+    a shuffled, randomly oriented copy give the same fields and cuts."""
+    g = inputs.erdos_renyi_gnm(60000, 600000, 11, "+1")
+    g.w = np.random.default_rng(4).choice(np.array([-2, -1, 1, 3], np.int8), g.m)
+    rng = np.random.default_rng(2)
+    perm = rng.permutation(g.m)
+    flip = rng.integers(0, 2, g.m).astype(bool)
+    src = np.where(flip, g.dst, g.src)[perm].astype(np.int32)
+    dst = np.where(flip, g.src, g.dst)[perm].astype(np.int32)
+    A = pbit.Graph(g.n, g.src, g.dst, g.w)
+    B = pbit.Graph(g.n, src, dst, g.w[perm])
+    assert A.info()["mean_s"] == B.info()["mean_s"]
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    assert A.info()["mean_s"] == oracle.mean_s(csr)
+    s = inputs.random_spins(g.n, 16, 5)
+    d = _dev(s)
+    fa = _host(A.fields(d))
+    assert np.array_equal(fa, _host(B.fields(d)))
+    assert np.array_equal(fa.astype(np.int64), oracle.fields(csr, s))
+    assert np.array_equal(A.cut(d), oracle.cut(g.src, g.dst, g.w, s))
