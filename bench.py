@@ -34,15 +34,15 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of each dominant kernel from one ncu capture (profiles/*.md), valid only while
 # the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
 TRAFFIC = {
-    "dense_persistent_kernel": {"bytes": 5209088 + 251392, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "64bcd12d262e1219",
+    "dense_persistent_kernel": {"bytes": 5234944 + 184064, "files": ["pbit_dense.cu", "pbit_device.cuh"],
+                                "sha": "36f00a53d801a421",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
-    "sparse_flow_kernel": {"bytes": 23933952 + 166513920,
+    "sparse_flow_kernel": {"bytes": 23511296 + 4966400,
                            "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
-                           "sha": "d0d85cb7e7a5e002", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
+                           "sha": "545363f66a551987", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
     # per launch of a 64-step chunk of all 64 instances
-    "batch_chunk_kernel": {"bytes": 810057216 + 1345518000, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
-                           "sha": "5403f544286cce7e", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
+    "batch_chunk_kernel": {"bytes": 811351552 + 1346066432, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
+                           "sha": "90f3bf29cc6398a2", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
 }
 
 
