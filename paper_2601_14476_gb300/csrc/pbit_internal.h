@@ -175,9 +175,10 @@ cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t*
 cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_ns, int* err, cudaStream_t s);
 // resident single-CTA anneal: all steps in one launch, spins in shared memory
 bool resident_fits(const Graph& g, int32_t T);
-// AUTO picks the single-CTA resident kernel only for small steps: one SM gathers about 2e10
-// neighbour-updates per second, and a multi-SM step costs about 12 µs (measured on GB300: G(800, 19176),
-// T = 16 runs 31 µs per step resident and 13 µs sparse), so the break-even is about 2.4e5 gathers.
+// AUTO picks the resident kernel (a cluster of 8 CTAs) only for small steps: the cluster gathers about
+// 1.1e11 neighbour-updates per second and a multi-SM sparse step costs at least about 12 µs (measured
+// on GB300: G(800, 19176), T = 16 runs 5.8 µs per step resident on the cluster, 32 µs on one CTA,
+// 12.4 µs sparse), so the break-even is about 1.3e6 gathers per step.
 bool resident_preferred(const Graph& g, int32_t T);
 cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,
                                    cudaStream_t s);

@@ -5,6 +5,7 @@
 // so the gather of neighbour j for a group of G consecutive trials is one
 // vector load (G = 16: int4, G = 4: 32-bit, G = 1: byte), coalesced across
 // the threads of a warp that share the node.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +19,8 @@
 
 namespace pbit {
 namespace {
+
+namespace cg = cooperative_groups;
 
 using namespace tile;
 
@@ -236,42 +239,54 @@ cudaError_t launch_flow_g(const FlowArgs& f, int device, cudaStream_t s) {
 }
 
 // -------------------------------------------------------------- resident ----
-// One CTA anneals one instance through steps [b, e) with both spin buffers in
-// shared memory; __syncthreads() is the synchronous-update barrier.
+// All steps [b, e) of one small instance in one launch, the spins held in
+// shared memory.  The CTAs of one thread-block cluster (8 when the cluster can
+// be placed, else 1) each keep a full copy of both spin buffers: each updates
+// the nodes it owns from its local copy and stores the new spins into its own
+// next buffer and into every peer's (distributed shared memory); the cluster
+// barrier (release / acquire) ends the step.  Nobody reads a buffer that is
+// being written: a step writes the buffers read in the step before, and every
+// CTA has finished reading those when it arrives at the barrier.
 constexpr int kResidentThreads = 512;
 constexpr size_t kResidentSmem = 200 * 1024;
+constexpr int kResidentCluster = 8;
 
 template <int G>
 __global__ void __launch_bounds__(kResidentThreads) resident_kernel(StepArgs a, int32_t step_begin, int32_t step_end) {
     extern __shared__ __align__(16) int8_t smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks(), r = (int)cluster.block_rank();
     const int64_t cells = (int64_t)a.n * a.T;
     int8_t* buf0 = smem;
     int8_t* buf1 = smem + ((cells + 15) / 16) * 16;
     for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) buf0[c] = a.in[c];
-    __syncthreads();
+    cluster.sync();  // every CTA runs (and holds the state) before any peer writes into it
     const int groups = a.T / G;
-    const int64_t items = (int64_t)a.n * groups;
+    const int node_lo = (int)((int64_t)a.n * r / C), node_hi = (int)((int64_t)a.n * (r + 1) / C);
+    const int64_t items = (int64_t)(node_hi - node_lo) * groups;
     int8_t* cur = buf0;
     int8_t* nxt = buf1;
     for (int32_t step = step_begin; step < step_end; ++step) {
         StepArgs sa = a;
         sa.step = step;
         for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
-            const int i = (int)(it / groups);
-            const int t0 = (int)(it - (int64_t)i * groups) * G;
+            const int i = node_lo + (int)(it / groups);
+            const int t0 = (int)(it - (int64_t)(i - node_lo) * groups) * G;
             int acc[G];
             gather_field<G>(a.row_ptr, a.col, a.J, cur, a.T, i, t0, acc);
             uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
-            load_group<G>(cur + (size_t)i * a.T + t0, oldw);
+            const size_t off = (size_t)i * a.T + t0;
+            load_group<G>(cur + off, oldw);
             decide_group<G>(sa, i, t0, acc, oldw, neww);
-            store_group<G>(nxt + (size_t)i * a.T + t0, neww);
+            store_group<G>(nxt + off, neww);
+            for (int q = 1; q < C; ++q) store_group<G>(cluster.map_shared_rank(nxt, (r + q) % C) + off, neww);
         }
-        __syncthreads();
+        cluster.sync();
         int8_t* tmp = cur;
         cur = nxt;
         nxt = tmp;
     }
-    for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) a.out[c] = cur[c];
+    for (int64_t c = (int64_t)node_lo * a.T + threadIdx.x; c < (int64_t)node_hi * a.T; c += blockDim.x) a.out[c] = cur[c];
 }
 
 template <int G>
@@ -281,9 +296,32 @@ cudaError_t launch_resident_g(const StepArgs& a, int32_t b, int32_t e, cudaStrea
     cudaError_t err = cudaFuncSetAttribute(resident_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)kResidentSmem);
     if (err != cudaSuccess) return err;
-    resident_kernel<G><<<1, kResidentThreads, smem, s>>>(a, b, e);
+    static const char* cl_env = std::getenv("PBIT_RESIDENT_CLUSTER");  // tests: 1 forces one CTA
+    const int want = cl_env ? std::max(1, std::min(kResidentCluster, std::atoi(cl_env))) : kResidentCluster;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)want, 1, 1);
+    cfg.blockDim = dim3(kResidentThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)want;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (want > 1 && cudaOccupancyMaxActiveClusters(&clusters, resident_kernel<G>, &cfg) == cudaSuccess && clusters >= 1) {
+        err = cudaLaunchKernelEx(&cfg, resident_kernel<G>, a, b, e);
+        count_launches(1);
+        return err;
+    }
+    (void)cudaGetLastError();
+    cfg.gridDim = dim3(1, 1, 1);
+    attr[0].val.clusterDim.x = 1;
+    err = cudaLaunchKernelEx(&cfg, resident_kernel<G>, a, b, e);
     count_launches(1);
-    return cudaGetLastError();
+    return err;
 }
 
 // ---------------------------------------------------------------- fields ----
@@ -588,7 +626,7 @@ cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_
 }
 
 bool resident_preferred(const Graph& g, int32_t T) {
-    return resident_fits(g, T) && (double)T * ((double)g.nnz + (double)g.n) <= 2.4e5;
+    return resident_fits(g, T) && (double)T * ((double)g.nnz + (double)g.n) <= 1.2e6;
 }
 
 bool resident_fits(const Graph& g, int32_t T) {

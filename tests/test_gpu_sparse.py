@@ -448,3 +448,34 @@ def test_large_graph_build_threads_any_order():
     assert np.array_equal(fa, _host(B.fields(d)))
     assert np.array_equal(fa.astype(np.int64), oracle.fields(csr, s))
     assert np.array_equal(A.cut(d), oracle.cut(g.src, g.dst, g.w, s))
+
+
+def test_resident_cluster_equals_single_cta_and_oracle(tmp_path):
+    """The resident kernel over a cluster of CTAs (spins exchanged through distributed shared memory)
+    gives exactly the single-CTA form's spins (forced in a child), on ragged trial counts, a graph
+    with fewer nodes than CTAs and a bias; and a lockstep step matches the oracle."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2601_14476_gb300 import inputs, pbit\n"
+        "outs = []\n"
+        "for g, T, S in ((inputs.erdos_renyi_gnm(800, 19176, 1, '+1'), 16, 120), (inputs.rgg_knn(700, 3, 3, 'pm1'), 3, 90),\n"
+        "                (inputs.torus_2d(3, 3, 1, 'pm1'), 64, 50), (inputs.erdos_renyi_gnm(300, 2000, 2, 'pm1'), 40, 77)):\n"
+        "    h = (np.mod(np.arange(g.n), 5) - 2).astype(np.int32)\n"
+        "    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h)\n"
+        "    var = inputs.variability(g.n, 4)\n"
+        "    outs.append(G.anneal(T, S, seed=6, variability=var, kernel=pbit.KERNEL_RESIDENT).cpu().numpy())\n"
+        "np.savez(%r, *outs)\n")
+    res = []
+    for k, extra in enumerate(({}, {"PBIT_RESIDENT_CLUSTER": "1"})):
+        path = str(tmp_path / f"r{k}.npz")
+        subprocess.run([sys.executable, "-c", code % path], check=True, env=dict(os.environ, **extra), timeout=300)
+        res.append(np.load(path))
+    for key in res[0].files:
+        assert np.array_equal(res[0][key], res[1][key]), key
+    g = inputs.rgg_knn(500, 9, 3, "pm1")
+    var = inputs.variability(g.n, 9)
+    dec, mis, worst = _lockstep(g, 20, 10, var, pbit.KERNEL_RESIDENT)
+    assert mis == 0 or worst < BAND
