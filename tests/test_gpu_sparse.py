@@ -479,3 +479,19 @@ def test_resident_cluster_equals_single_cta_and_oracle(tmp_path):
     var = inputs.variability(g.n, 9)
     dec, mis, worst = _lockstep(g, 20, 10, var, pbit.KERNEL_RESIDENT)
     assert mis == 0 or worst < BAND
+
+
+def test_resident_resume_in_place():
+    """Cluster-resident kernel: a run split into resumed segments, in place (input = output buffer),
+    equals the whole run, for odd and even segment lengths and an empty range."""
+    g = inputs.erdos_renyi_gnm(500, 4000, 12, "pm1")
+    var = inputs.variability(g.n, 12)
+    G = pbit.Graph.from_inputs(g)
+    T, S = 24, 61
+    full = _host(G.anneal(T, S, seed=7, variability=var, kernel=pbit.KERNEL_RESIDENT))
+    a = G.anneal(T, S, step_end=20, seed=7, variability=var, kernel=pbit.KERNEL_RESIDENT)
+    for lo, hi in ((20, 33), (33, 33), (33, S)):
+        p, keep = pbit.make_params(T, S, step_begin=lo, step_end=hi, seed=7, variability=var,
+                                   kernel=pbit.KERNEL_RESIDENT)
+        pbit.pbit_anneal(G.handle, p, a, a)
+    assert np.array_equal(_host(a), full)
