@@ -47,12 +47,14 @@ TRAFFIC = {
 
 
 def batch_traffic(tuning, steps: int):
-    """DRAM bytes of one batched run (steps / chunk launches), from the per-chunk capture."""
+    """DRAM bytes of one batched run, scaled from the capture of one 64-step chunk by the number of
+    steps (the traffic is per step: the spin buffers' write-back and re-read), whatever chunk length
+    the autotuner picked."""
     per_chunk = traffic_for("batch_chunk_kernel")
     chunk = TRAFFIC["batch_chunk_kernel"]["chunk_steps"]
-    if per_chunk is None or tuning.get("chunk_steps") != chunk or steps % chunk:
+    if per_chunk is None:
         return None
-    return per_chunk * (steps // chunk)
+    return int(per_chunk * steps / chunk)
 
 
 def sparse_tile_kernel(g, T: int, launches_per_anneal: float, steps: int) -> str:
