@@ -37,9 +37,9 @@ TRAFFIC = {
     "dense_persistent_kernel": {"bytes": 5234944 + 184064, "files": ["pbit_dense.cu", "pbit_device.cuh"],
                                 "sha": "36f00a53d801a421",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
-    "sparse_flow_kernel": {"bytes": 23394048 + 4725760,
-                           "files": ["pbit_tile.cuh", "pbit_sparse.cu", "pbit_device.cuh"],
-                           "sha": "c7acd82a74a835e3", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
+    "sparse_flow_kernel": {"bytes": 23335680 + 5099264,
+                           "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
+                           "sha": "5fedf916d58b284d", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
     # per launch of a 64-step chunk of all 64 instances
     "batch_chunk_kernel": {"bytes": 811351552 + 1346066432, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
                            "sha": "90f3bf29cc6398a2", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
