@@ -97,6 +97,42 @@ def workload(name: str):
     raise SystemExit(f"unknown config {name}")
 
 
+def variant_args(args, w) -> dict:
+    """make_params keywords of the pSA variant / timing model selected on the command line (empty for
+    plain pSA); the workload's name records the choice."""
+    from paper_2601_14476_gb300 import pbit
+    alg = {"psa": pbit.ALG_PSA, "spsa": pbit.ALG_SPSA, "tapsa": pbit.ALG_TAPSA}[args.algorithm]
+    if alg == pbit.ALG_PSA and args.t_res <= 0:
+        return {}
+    if args.config not in ("sparse", "plain"):
+        raise SystemExit("the pSA variants and the timing model run on the sparse configs")
+    out = {"algorithm": alg, "stall_prob": args.stall_prob, "window": args.window}
+    if alg != pbit.ALG_PSA:
+        w.name += f"_{args.algorithm}" + (f"_w{args.window}" if alg == pbit.ALG_TAPSA else f"_p{args.stall_prob:g}")
+    if args.t_res > 0:
+        out["t_res"] = args.t_res
+        out["nu_dev"] = inputs.timing_deviation(w.graph.n, w.seed, args.s_nu)
+        w.name += f"_tres{args.t_res}_snu{args.s_nu:g}"
+    return out
+
+
+def variant_bytes(variant: dict, mean_deg: float) -> float:
+    """Algorithmic bytes per (node, trial, sub-step) update of a variant: the pSA gather (deg
+    neighbour bytes + own + written) plus the carried state (SpSA: the float32 input read and
+    written; TApSA: the int16 window read and one field written); with the timing model, idle
+    updates only copy their spin (2 bytes), and a node is active on a fraction f of sub-steps."""
+    from paper_2601_14476_gb300 import pbit
+    alg = variant.get("algorithm", pbit.ALG_PSA)
+    state = 8.0 if alg == pbit.ALG_SPSA else (2.0 * (variant.get("window", 4) + 1) if alg == pbit.ALG_TAPSA else 0.0)
+    active = mean_deg + 2.0 + state
+    t_res = variant.get("t_res", 0)
+    if t_res <= 0:
+        return active
+    nu = np.maximum(1, np.round(t_res * (1.0 + np.asarray(variant["nu_dev"], np.float64))))
+    f = float(np.mean(1.0 / nu))
+    return f * active + (1.0 - f) * 2.0
+
+
 def workload_config(w) -> dict:
     """The keys that name a single-instance workload, shared by both bench arms."""
     g = w.graph
@@ -199,7 +235,7 @@ def _oracle_sample(job):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(w, budget_s: float = 12.0, kind: str | None = None, all_cores: bool = True):
+def cpu_baseline(w, budget_s: float = 12.0, kind: str | None = None, all_cores: bool = True, variant=None):
     """Time the oracle (single-threaded FP64) on a bounded sample: all trials, first k schedule steps.
 
     With all_cores, every host core also runs its own copy of the same sample at once (spawned
@@ -210,19 +246,30 @@ def cpu_baseline(w, budget_s: float = 12.0, kind: str | None = None, all_cores: 
     csr = oracle.Csr(g.n, g.src, g.dst, g.w)
     tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
     s0 = oracle.init_spins(g.n, w.trials, w.seed, w.instance)
+    v = dict(variant or {})
+
+    def run(k):  # the first k (sub-)steps
+        if v:
+            oracle.anneal_variant(csr, s0, tab, w.seed, w.instance, algorithm=v.get("algorithm", 0),
+                                  stall_prob=v.get("stall_prob", 0.5), window=v.get("window", 4),
+                                  t_res=v.get("t_res", 0), nu_dev=v.get("nu_dev"), variability=w.var, q_end=k)
+        else:
+            oracle.anneal(csr, s0, tab, w.seed, w.instance, variability=w.var, step_end=k)
+
+    total = w.steps * max(1, v.get("t_res", 0))
     t0 = time.perf_counter()
-    oracle.anneal(csr, s0, tab, w.seed, w.instance, variability=w.var, step_end=1)
+    run(1)
     one = max(time.perf_counter() - t0, 1e-6)
-    k = int(max(1, min(w.steps, budget_s / one)))
+    k = int(max(1, min(total, budget_s / one)))
     t0 = time.perf_counter()
-    oracle.anneal(csr, s0, tab, w.seed, w.instance, variability=w.var, step_end=k)
+    run(k)
     dt = time.perf_counter() - t0
     upd = g.n * w.trials * k
     out = {"value": upd / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
-           "sample": f"{w.name}: all {w.trials} trials, schedule steps [0,{k}) of {w.steps} "
+           "sample": f"{w.name}: all {w.trials} trials, (sub-)steps [0,{k}) of {total} "
                      f"({upd:.3g} updates, {dt:.1f} s)"}
     ncores = os.cpu_count() or 1
-    if all_cores and kind and ncores > 1:
+    if all_cores and kind and ncores > 1 and not v:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(ncores) as pool:
             pool.map(_oracle_sample, [(kind, 1)] * ncores)  # build each process's case, warm up
@@ -234,19 +281,19 @@ def cpu_baseline(w, budget_s: float = 12.0, kind: str | None = None, all_cores: 
     return out
 
 
-def run_reference(args, w):
+def run_reference(args, w, variant=None):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     t_all = []
     base = None
     for it in range(args.warmup + args.steps):
-        b = cpu_baseline(w, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        b = cpu_baseline(w, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)), variant=variant)
         if it >= args.warmup:
             t_all.append(b["value"])
             base = b
     val = float(np.mean(t_all))
-    upd_run = w.graph.n * w.trials * w.steps
+    upd_run = w.graph.n * w.trials * w.steps * max(1, (variant or {}).get("t_res", 0))
     line = {"impl": "reference", "metric": "spin-updates/s", "value": val, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * upd_run / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -482,6 +529,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--anneal-steps", type=int, default=0,
                     help="shorten the schedule (profiling captures only; such a line is not a bench value)")
+    ap.add_argument("--algorithm", default="psa", choices=["psa", "spsa", "tapsa"],
+                    help="pSA variant of the Methods section (sparse / plain configs)")
+    ap.add_argument("--stall-prob", type=float, default=0.5, help="SpSA stall probability")
+    ap.add_argument("--window", type=int, default=4, help="TApSA window")
+    ap.add_argument("--t-res", type=int, default=0, help="timing model: sub-steps per cycle (0: off)")
+    ap.add_argument("--s-nu", type=float, default=0.1, help="timing model: spread of the period deviation")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -491,8 +544,9 @@ def main():
     if args.anneal_steps > 0:
         w.steps = args.anneal_steps
         w.name += f"_first{args.anneal_steps}steps"
+    variant = variant_args(args, w)
     if args.impl == "reference":
-        return run_reference(args, w)
+        return run_reference(args, w, variant)
 
     import torch
     from paper_2601_14476_gb300 import pbit
@@ -517,7 +571,8 @@ def main():
     cuts = torch.empty(T, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     params, keep = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
-                                    kernel=kernel, variability=w.var, stream=stream)
+                                    kernel=kernel, variability=w.var, stream=stream, **variant)
+    sub = max(1, variant.get("t_res", 0))  # updates per cycle and node-trial (timing model: sub-steps)
 
     def one_run():
         pbit.pbit_anneal(G.handle, params, None, spins)
@@ -540,7 +595,7 @@ def main():
         torch.cuda.synchronize()
     launches = pbit.pbit_launch_count() - launches0
     ms = [a.elapsed_time(b) for a, b in ev]
-    upd_run = g.n * T * S
+    upd_run = g.n * T * S * sub
     value, ms_step = job_throughput(dist, upd_run, float(np.mean(ms)), world)
 
     # dominant kernel: the anneal itself (one persistent launch for the dense path, one launch per step
@@ -570,23 +625,28 @@ def main():
                     "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
     else:
         kname = sparse_tile_kernel(g, T, anneal_launches, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
-        launches_main = S if kname in ("sparse_warp_kernel", "sparse_step_kernel") else 1
+        if variant:
+            kname = "sparse_variant_kernel"
+        launches_main = S * sub if kname in ("sparse_warp_kernel", "sparse_step_kernel", "sparse_variant_kernel") else 1
         per_launch_ms = anneal_ms / launches_main
         mean_deg = 2.0 * g.m / g.n
         # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
-        alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
+        # (variants: plus their carried state, see variant_bytes)
+        alg_bytes = g.n * T * variant_bytes(variant, mean_deg) * (S * sub / launches_main)
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"],
                     "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,
                     "kernel": kname,
                     "peak_source": pk["source"],
-                    "per_launch": f"(deg+2) bytes x n*T updates per step; {launches_main} launches"}
+                    "per_launch": (f"{variant_bytes(variant, mean_deg):.2f} bytes x n*T updates per sub-step; "
+                                   f"{launches_main} launches" if variant else
+                                   f"(deg+2) bytes x n*T updates per step; {launches_main} launches")}
     roofline["kernel_ms_per_anneal"] = anneal_ms
 
     # end to end through the C ABI from host buffers: graph upload, anneal, cut to host
     e2e_ms = []
-    h2d = g.m * (4 + 4 + 1) + (3 * g.n * 4 if w.var else 0) + S * 4
+    h2d = g.m * (4 + 4 + 1) + (3 * g.n * 4 if w.var else 0) + S * 4 + (4 * g.n if "nu_dev" in variant else 0)
     d2h = T * 8
     for it in range(0 if args.no_e2e else 2 + args.steps):
         torch.cuda.synchronize()
@@ -594,7 +654,7 @@ def main():
         G2 = pbit.Graph.from_inputs(g, dense=(args.config == "dense"))
         out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
         p2, keep2 = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
-                                     kernel=kernel, variability=w.var, stream=stream)
+                                     kernel=kernel, variability=w.var, stream=stream, **variant)
         pbit.pbit_anneal(G2.handle, p2, None, out)
         host_cuts = pbit.pbit_cut(G2.handle, out, T, stream)
         torch.cuda.synchronize()
@@ -612,7 +672,7 @@ def main():
         return
     cb = None
     if not args.no_cpu_baseline and world == 1:
-        cb = cpu_baseline(w, kind=args.config)
+        cb = cpu_baseline(w, kind=args.config, variant=variant)
     line = {
         "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -149,6 +149,12 @@ def variability(n: int, seed: int, s_intensity: float = 0.1, s_offset: float = 0
     }
 
 
+def timing_deviation(n: int, seed: int, s_nu: float = 0.1) -> np.ndarray:
+    """Per-node deviation of the update period for the paper's timing model: nu_i ~ N(0, s_nu^2)."""
+    rng = np.random.default_rng([0x6E75, seed])
+    return (s_nu * rng.standard_normal(n)).astype(np.float32)
+
+
 def random_spins(n: int, T: int, seed: int) -> np.ndarray:
     """Uniform +-1 trial-major spins, for tests that start from a given state."""
     rng = np.random.default_rng([0x7370, seed])
