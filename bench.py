@@ -113,31 +113,37 @@ def variant_args(args, w) -> dict:
         out["t_res"] = args.t_res
         out["nu_dev"] = inputs.timing_deviation(w.graph.n, w.seed, args.s_nu)
         w.name += f"_tres{args.t_res}_snu{args.s_nu:g}"
+        w.updates = variant_work(out, w.graph, w.trials, w.steps * args.t_res)[0]
     return out
 
 
-def variant_bytes(variant: dict, mean_deg: float) -> float:
-    """Algorithmic bytes per (node, trial, sub-step) update of a variant: the pSA gather (deg
-    neighbour bytes + own + written) plus the carried state (SpSA: the float32 input read and
-    written; TApSA: the int16 window read and one field written); with the timing model, idle
-    updates only copy their spin (2 bytes), and a node is active on a fraction f of sub-steps."""
+def variant_work(variant: dict, g, T: int, Q: int):
+    """(spin updates, algorithmic bytes) of the first Q (sub-)steps of a variant on graph g with T trials.
+
+    An update of node i reads deg_i neighbour bytes and its own, writes one, and carries its state
+    (SpSA: the float32 input read and written, 8 B; TApSA: window - 1 int16 fields read, one written,
+    2 window B).  Timing model (period nu_i = max(1, round(t_res (1 + nu_dev_i)))): node i updates at
+    the sub-steps q % nu_i == 0 only; an idle node copies its spin (2 B) where the output buffer lacks
+    it: at sub-step 1, and at every later sub-step right after one of its updates."""
     from paper_2601_14476_gb300 import pbit
     alg = variant.get("algorithm", pbit.ALG_PSA)
-    state = 8.0 if alg == pbit.ALG_SPSA else (2.0 * (variant.get("window", 4) + 1) if alg == pbit.ALG_TAPSA else 0.0)
-    active = mean_deg + 2.0 + state
+    state = 8 if alg == pbit.ALG_SPSA else (2 * variant.get("window", 4) if alg == pbit.ALG_TAPSA else 0)
+    deg = (np.bincount(g.src, minlength=g.n) + np.bincount(g.dst, minlength=g.n)).astype(np.int64)
     t_res = variant.get("t_res", 0)
     if t_res <= 0:
-        return active
-    nu = np.maximum(1, np.round(t_res * (1.0 + np.asarray(variant["nu_dev"], np.float64))))
-    f = float(np.mean(1.0 / nu))
-    return f * active + (1.0 - f) * 2.0
+        return g.n * T * Q, T * Q * float(deg.sum() + g.n * (2 + state))
+    dev = np.zeros(g.n) if variant.get("nu_dev") is None else np.asarray(variant["nu_dev"], np.float32)
+    nu = np.maximum(1, np.floor(t_res * (1.0 + dev.astype(np.float64)) + 0.5)).astype(np.int64)
+    due = (Q + nu - 1) // nu
+    copies = np.where(nu > 1, (1 + (Q - 2) // nu) if Q >= 2 else 0, 0)
+    return T * int(due.sum()), T * float((due * (deg + 2 + state)).sum() + 2 * copies.sum())
 
 
 def workload_config(w) -> dict:
     """The keys that name a single-instance workload, shared by both bench arms."""
     g = w.graph
     return {"workload": w.name, "n": g.n, "edges": g.m, "trials": w.trials, "anneal_steps": w.steps,
-            "variability": w.var is not None, "updates_per_step": g.n * w.trials * w.steps}
+            "variability": w.var is not None, "updates_per_step": getattr(w, "updates", g.n * w.trials * w.steps)}
 
 
 def peaks():
@@ -264,7 +270,7 @@ def cpu_baseline(w, budget_s: float = 12.0, kind: str | None = None, all_cores: 
     t0 = time.perf_counter()
     run(k)
     dt = time.perf_counter() - t0
-    upd = g.n * w.trials * k
+    upd = variant_work(v, g, w.trials, k)[0] if v else g.n * w.trials * k
     out = {"value": upd / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
            "sample": f"{w.name}: all {w.trials} trials, (sub-)steps [0,{k}) of {total} "
                      f"({upd:.3g} updates, {dt:.1f} s)"}
@@ -293,7 +299,7 @@ def run_reference(args, w, variant=None):
             t_all.append(b["value"])
             base = b
     val = float(np.mean(t_all))
-    upd_run = w.graph.n * w.trials * w.steps * max(1, (variant or {}).get("t_res", 0))
+    upd_run = getattr(w, "updates", w.graph.n * w.trials * w.steps)
     line = {"impl": "reference", "metric": "spin-updates/s", "value": val, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * upd_run / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -595,7 +601,7 @@ def main():
         torch.cuda.synchronize()
     launches = pbit.pbit_launch_count() - launches0
     ms = [a.elapsed_time(b) for a, b in ev]
-    upd_run = g.n * T * S * sub
+    upd_run = getattr(w, "updates", g.n * T * S)  # the timing model counts the updates of due nodes only
     value, ms_step = job_throughput(dist, upd_run, float(np.mean(ms)), world)
 
     # dominant kernel: the anneal itself (one persistent launch for the dense path, one launch per step
@@ -626,20 +632,25 @@ def main():
     else:
         kname = sparse_tile_kernel(g, T, anneal_launches, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
         if variant:
-            kname = "sparse_variant_kernel"
-        launches_main = S * sub if kname in ("sparse_warp_kernel", "sparse_step_kernel", "sparse_variant_kernel") else 1
+            kname = "sparse_variant_words_kernel" if T % 128 == 0 else "sparse_variant_kernel"
+        launches_main = S if kname in ("sparse_warp_kernel", "sparse_step_kernel") else 1
+        if variant:
+            launches_main = anneal_launches
         per_launch_ms = anneal_ms / launches_main
         mean_deg = 2.0 * g.m / g.n
         # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
-        # (variants: plus their carried state, see variant_bytes)
-        alg_bytes = g.n * T * variant_bytes(variant, mean_deg) * (S * sub / launches_main)
+        # (variants: plus their carried state and the timing model's copies, see variant_work)
+        if variant:
+            alg_bytes = variant_work(variant, g, T, S * sub)[1] / launches_main
+        else:
+            alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"],
                     "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,
                     "kernel": kname,
                     "peak_source": pk["source"],
-                    "per_launch": (f"{variant_bytes(variant, mean_deg):.2f} bytes x n*T updates per sub-step; "
+                    "per_launch": (f"variant bytes of the whole run (deg+2+state per update, 2 per copy) / "
                                    f"{launches_main} launches" if variant else
                                    f"(deg+2) bytes x n*T updates per step; {launches_main} launches")}
     roofline["kernel_ms_per_anneal"] = anneal_ms

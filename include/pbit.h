@@ -180,8 +180,10 @@ typedef struct {
 
 typedef enum { PBIT_ALG_PSA = 0, PBIT_ALG_SPSA = 1, PBIT_ALG_TAPSA = 2 } pbit_algorithm;
 
-/* Bytes of variant state for n nodes and T trials: SpSA 4*n*T (float32 last input), TApSA
- * 2*window*n*T (int16 last fields), pSA 0.  Zero-filled memory is the state before step 0. */
+/* Bytes of variant state for n nodes and T trials: SpSA 4*n*T (float32 last input, [n][T]), TApSA
+ * 2*window*n*T (int16 last fields, [window][n][T], slot q % window written at sub-step q), pSA 0.
+ * Zero-filled memory is the state before step 0.  TApSA needs every field to fit int16
+ * (|h_i| + sum_j |J_ij| <= 32767), else pbit_anneal returns PBIT_E_UNSUPPORTED. */
 size_t pbit_variant_state_bytes(int32_t n, int32_t trials, int32_t algorithm, int32_t window);
 
 /* Fill `p` with defaults: T=1, S=1, whole schedule, I0 0.1..10 normalised, SCALED, AUTO, pSA. */

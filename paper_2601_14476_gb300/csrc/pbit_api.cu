@@ -500,6 +500,8 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     if (p->algorithm == PBIT_ALG_TAPSA && (p->window < 1 || p->window > 64))
         return fail(PBIT_E_INVALID, "anneal: window outside 1..64");
     const bool is_var = p->algorithm != PBIT_ALG_PSA || p->t_res > 0;
+    if (p->algorithm == PBIT_ALG_TAPSA && g->max_abs_field > 32767)
+        return fail(PBIT_E_UNSUPPORTED, "anneal: TApSA keeps fields as int16; |h_i| + sum_j |J_ij| exceeds 32767");
     if (p->algorithm != PBIT_ALG_PSA && !p->state && b != 0)
         return fail(PBIT_E_INVALID, "anneal: resuming SpSA/TApSA needs the state buffer of the earlier run");
     pbit_status st = check_device(g);
@@ -563,6 +565,7 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         a.par.thr = d;
     }
     // variant state and timing periods
+    PeriodBuckets buckets;
     a.alg = p->algorithm;
     a.window = p->window < 1 ? 1 : p->window;
     a.t_res = p->t_res;
@@ -576,6 +579,10 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         int32_t* d = nullptr;
         if ((st = cb.put(&d, nu.data(), nu.size())) != PBIT_OK) return st;
         a.nu = d;
+        build_period_buckets(nu, buckets);
+        int32_t* dp = nullptr;
+        if ((st = cb.put(&dp, buckets.host_perm.data(), buckets.host_perm.size())) != PBIT_OK) return st;
+        buckets.perm = dp;
     }
     if (a.alg != PBIT_ALG_PSA) {
         const size_t sb = pbit_variant_state_bytes(g->n, T, a.alg, a.window);
@@ -688,7 +695,12 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         a.step = b + j;
         a.in = cur;
         a.out = dst;
-        PBIT_CUDA_TRY(launch_sparse_step(a, s, variant));
+        if (is_variant(a)) {
+            a.carry = j >= 2 ? 1 : 0;  // dst holds the state of sub-step b + j - 2 from the second write on
+            PBIT_CUDA_TRY(launch_variant_step(a, &buckets, s, variant));
+        } else {
+            PBIT_CUDA_TRY(launch_sparse_step(a, s, variant));
+        }
         cur = dst;
     }
     return PBIT_OK;

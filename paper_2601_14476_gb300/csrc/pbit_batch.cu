@@ -225,6 +225,8 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
         return fail(PBIT_E_INVALID, "instance: bad algorithm parameters");
     if ((p->algorithm != PBIT_ALG_PSA || p->t_res > 0) && sb != 0)
         return fail(PBIT_E_INVALID, "instance: variants start at step 0 in batches and servers");
+    if (p->algorithm == PBIT_ALG_TAPSA && g.max_abs_field > 32767)
+        return fail(PBIT_E_UNSUPPORTED, "instance: TApSA keeps fields as int16; |h_i| + sum_j |J_ij| exceeds 32767");
     pbit_status st;
     std::vector<float> tab;
     if ((st = build_schedule(g, p->i0_min, p->i0_max, p->i0_normalize, S, tab)) != PBIT_OK) return st;

@@ -122,6 +122,8 @@ struct StepArgs {
     const int32_t* nu;        // [n] update period in sub-steps (timing model)
     float* Iprev;             // SpSA state [n][T]: the last input
     int16_t* ring;            // TApSA state [window][n][T]: the last fields
+    int32_t carry;            // timing model: out holds the state of sub-step step - 2 (see pbit_variant.cu)
+    const int32_t* perm;      // timing model: nodes grouped by period (set per launch by the word tile)
     // item -> node for the warp-table tile: node = (item * grp_m) >> grp_s = item / (T / G),
     // exact for item < 2^31 (filled by set_group_divisor for the G the launcher picks)
     uint64_t grp_m;
@@ -155,6 +157,15 @@ cudaError_t launch_sparse_flow(const Graph& g, StepArgs a, int32_t k, const int8
                                unsigned* tile_done, unsigned* step_done, unsigned long long* next,
                                SparseVariant v, cudaStream_t s);
 __host__ __device__ inline bool is_variant(const StepArgs& a) { return a.alg != 0 || a.t_res > 0; }
+// The variants' coalesced word tile (pbit_variant.cu).  PeriodBuckets groups the nodes by update
+// period so that a sub-step with `carry` launches warps only for the nodes due at q or q - 1.
+struct PeriodBuckets {
+    const int32_t* perm = nullptr;             // device [n]: node ids sorted by period
+    std::vector<int32_t> host_perm;
+    std::vector<int32_t> period, start, len;   // per distinct period: its run [start, start + len) of perm
+};
+void build_period_buckets(const std::vector<int32_t>& nu, PeriodBuckets& pb);
+cudaError_t launch_variant_step(const StepArgs& a, const PeriodBuckets* pb, cudaStream_t s, SparseVariant v);
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
 cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
                               cudaStream_t s);

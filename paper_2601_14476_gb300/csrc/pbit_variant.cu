@@ -1,0 +1,298 @@
+// The pSA variants of the Methods section (SpSA: a stalled p-bit keeps its
+// last input; TApSA: the input is the mean of the last `window` fields) and
+// the paper's period timing model (node i updates only at the sub-steps q
+// with q % nu_i == 0), one launch per (sub-)step, in a coalesced word tile.
+//
+// Tile: a warp owns a span of 128 * NW consecutive trials of one node; lane l
+// takes the 4-trial words l, l + 32, ... of the span.  So every access of a
+// warp for one word index is one contiguous run: 128 B of spins for the node
+// and for each neighbour, 512 B of SpSA float32 inputs, 256 B of TApSA int16
+// fields per ring slot.  The state keeps its plain [n][T] (SpSA) and
+// [window][n][T] (TApSA) layout.
+//
+// Timing model: a node that is not due copies its spins to the output buffer,
+// but only when that buffer does not already hold them.  In the Jacobi
+// rotation the output of sub-step q holds the state of sub-step q - 2
+// (`carry`), which differs from the state of q - 1 only for the nodes due at
+// q - 1, so with `carry` a sub-step touches the nodes due at q or q - 1 only.
+// The host groups the nodes by period (PeriodBuckets) and launches warps for
+// those two groups of periods alone.
+#include "pbit_internal.h"
+#include "pbit_device.cuh"
+#include "pbit_tile.cuh"
+
+#include <algorithm>
+#include <cstdlib>
+#include <numeric>
+
+namespace pbit {
+namespace {
+
+using tile::sign_bytes;
+using tile::variant_x;
+
+constexpr int kVBlock = 256;
+constexpr int kMaxRanges = 32;
+
+struct VariantLaunch {
+    StepArgs a;
+    uint32_t spans;           // spans per node: T / (128 * NW)
+    uint64_t span_m;          // local warp -> node: (w * span_m) >> span_s = w / spans
+    int32_t span_s;
+    int32_t nranges;          // 0: warps cover all nodes in order; else the perm ranges below
+    uint32_t warps;           // warps of the launch
+    int32_t rstart[kMaxRanges];     // first perm position of range r
+    uint32_t rwarp_end[kMaxRanges]; // prefix sums of the warps of ranges 0..r
+};
+
+// Division by d >= 1 for dividends below 2^31 (Granlund-Montgomery).
+void magic_divisor(uint32_t d, uint64_t& m, int32_t& s) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    m = ((1ull << (32 + l)) / d) + 1;
+    s = 32 + l;
+}
+
+__device__ __forceinline__ uint32_t ld32(const int8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ void st32(int8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+
+// WIN: the TApSA window when it is 4 (the paper's; its other-slot loads unrolled), else 0
+template <int NW, bool UNIT, int WIN>
+__global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __grid_constant__ VariantLaunch L) {
+    const StepArgs& a = L.a;
+    const uint32_t warp = (blockIdx.x * (uint32_t)kVBlock + threadIdx.x) >> 5;
+    const int lane = (int)(threadIdx.x & 31u);
+    if (warp >= L.warps) return;
+    uint32_t local = warp;
+    int32_t first = 0;
+    if (L.nranges > 0) {
+        int r = 0;
+        while (r + 1 < L.nranges && warp >= L.rwarp_end[r]) ++r;
+        local = warp - (r ? L.rwarp_end[r - 1] : 0u);
+        first = L.rstart[r];
+    }
+    const uint32_t nl = (uint32_t)(((unsigned long long)local * L.span_m) >> L.span_s);
+    const uint32_t sidx = local - nl * L.spans;
+    const int i = L.nranges > 0 ? __ldg(a.perm + first + (int)nl) : (int)nl;
+    const int T = a.T;
+    const uint32_t q = (uint32_t)a.step;
+    const int tb = (int)sidx * (128 * NW) + 4 * lane;  // trial of word 0; word k at tb + 128 k
+    const size_t row = (size_t)i * T;
+    if (a.t_res > 0) {
+        const uint32_t nu = (uint32_t)__ldg(a.nu + i);
+        if (q % nu != 0u) {
+            if (!a.carry || (q - 1u) % nu == 0u) {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) st32(a.out + row + tb + 128 * k, ld32(a.in + row + tb + 128 * k));
+            }
+            return;
+        }
+    }
+    const float I0 = __ldg(a.i0_table + (a.t_res > 0 ? q / (uint32_t)a.t_res : q));
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+    // the carried state first, so that its loads are in flight during the gather:
+    // SpSA the last inputs, TApSA the sum of the ring slots other than q % window
+    const size_t plane = (size_t)a.n * T;
+    const int slot = a.alg == 2 ? (int)(q % (uint32_t)a.window) : 0;
+    float4 prev[NW];
+    int osum[4 * NW];
+#pragma unroll
+    for (int k = 0; k < 4 * NW; ++k) osum[k] = 0;
+    if (a.alg == 1) {
+#pragma unroll
+        for (int k = 0; k < NW; ++k) prev[k] = *reinterpret_cast<const float4*>(a.Iprev + row + tb + 128 * k);
+    } else if (a.alg == 2) {
+        const auto add_slot = [&](int w) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const uint2 v = *reinterpret_cast<const uint2*>(a.ring + (size_t)w * plane + row + tb + 128 * k);
+                osum[4 * k] += (int)(int16_t)(v.x & 0xFFFFu);
+                osum[4 * k + 1] += (int)(int16_t)(v.x >> 16);
+                osum[4 * k + 2] += (int)(int16_t)(v.y & 0xFFFFu);
+                osum[4 * k + 3] += (int)(int16_t)(v.y >> 16);
+            }
+        };
+        if constexpr (WIN > 0) {
+#pragma unroll
+            for (int u = 1; u < WIN; ++u) add_slot(slot + u < WIN ? slot + u : slot + u - WIN);
+        } else {
+            for (int u = 1; u < a.window; ++u) add_slot(slot + u < a.window ? slot + u : slot + u - a.window);
+        }
+    }
+    // exact fields D = h_i + sum_j J_ij s_j (Eq. 1)
+    int D[4 * NW];
+    if constexpr (UNIT) {
+        // +-1 weights: count 2 per neighbour with J_ij s_j = -1 (bit 1 of the spin byte, flipped for J = -1)
+        uint32_t cnt2[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) cnt2[k] = 0;
+        for (int e = rb; e < re; ++e) {
+            const int8_t* pj = a.in + (size_t)__ldg(a.col + e) * T + tb;
+            const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) cnt2[k] += (ld32(pj + 128 * k) & 0x02020202u) ^ flip;
+        }
+        const int base = hi + (re - rb);
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) D[4 * k + b] = base - (int)((cnt2[k] >> (8 * b)) & 0xFFu);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4 * NW; ++k) D[k] = hi;
+        for (int e = rb; e < re; ++e) {
+            const int8_t* pj = a.in + (size_t)__ldg(a.col + e) * T + tb;
+            const int w = __ldg(a.J + e);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const uint32_t v = ld32(pj + 128 * k);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) D[4 * k + b] += w * tile::sbyte(v, b);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const int t = tb + 128 * k;
+        const size_t cell = row + t;
+        float I[4];
+        if (a.alg == 1) {
+            // SpSA: stall draw of trial t + b = word b of Philox(node, q, t / 4, instance ^ 2^31)
+            const uint4 sw = philox((uint32_t)i, q, (uint32_t)t >> 2, a.instance ^ 0x80000000u, a.seed_lo, a.seed_hi);
+            I[0] = (sw.x >> 8) < a.stall_thr ? prev[k].x : __fmul_rn(I0, (float)D[4 * k]);
+            I[1] = (sw.y >> 8) < a.stall_thr ? prev[k].y : __fmul_rn(I0, (float)D[4 * k + 1]);
+            I[2] = (sw.z >> 8) < a.stall_thr ? prev[k].z : __fmul_rn(I0, (float)D[4 * k + 2]);
+            I[3] = (sw.w >> 8) < a.stall_thr ? prev[k].w : __fmul_rn(I0, (float)D[4 * k + 3]);
+            *reinterpret_cast<float4*>(a.Iprev + cell) = make_float4(I[0], I[1], I[2], I[3]);
+        } else if (a.alg == 2) {
+            // TApSA: ring slot q % window <- D (int16); I = I0 * (sum of the ring) / window
+            int16_t d16[4];
+            int sum[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                d16[b] = (int16_t)D[4 * k + b];
+                sum[b] = osum[4 * k + b] + d16[b];
+            }
+            *reinterpret_cast<uint2*>(a.ring + (size_t)slot * plane + cell) =
+                make_uint2((uint32_t)(uint16_t)d16[0] | ((uint32_t)(uint16_t)d16[1] << 16),
+                           (uint32_t)(uint16_t)d16[2] | ((uint32_t)(uint16_t)d16[3] << 16));
+#pragma unroll
+            for (int b = 0; b < 4; ++b) I[b] = __fmul_rn(I0, __fdiv_rn((float)sum[b], (float)a.window));
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) I[b] = __fmul_rn(I0, (float)D[4 * k + b]);
+        }
+        // decisions (Eq. 6): candidate +1 iff r-word k-value < kthr, update iff u-word < thr
+        uint4 r0, r1;
+        philox_pair((uint32_t)i, q, (uint32_t)t >> 1, (uint32_t)(t + 2) >> 1, a.instance, a.seed_lo, a.seed_hi, r0,
+                    r1);
+        const uint32_t k0 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[0]));
+        const uint32_t k1 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[1]));
+        const uint32_t k2 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[2]));
+        const uint32_t k3 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[3]));
+        const uint32_t S = sign_bytes((r0.x >> 8) - k0, (r0.z >> 8) - k1, (r1.x >> 8) - k2, (r1.z >> 8) - k3);
+        const uint32_t U = sign_bytes((r0.y >> 8) - thr, (r0.w >> 8) - thr, (r1.y >> 8) - thr, (r1.w >> 8) - thr);
+        const uint32_t old = ld32(a.in + cell);
+        st32(a.out + cell, ((U & ~S) | (~U & old)) | 0x01010101u);
+    }
+}
+
+template <int NW, bool UNIT>
+cudaError_t launch_words(const VariantLaunch& L, cudaStream_t s) {
+    if (L.warps == 0) return cudaSuccess;
+    const uint64_t blocks = ((uint64_t)L.warps * 32 + kVBlock - 1) / kVBlock;
+    if (L.a.alg == 2 && L.a.window == 4)
+        sparse_variant_words_kernel<NW, UNIT, 4><<<(unsigned)blocks, kVBlock, 0, s>>>(L);
+    else
+        sparse_variant_words_kernel<NW, UNIT, 0><<<(unsigned)blocks, kVBlock, 0, s>>>(L);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+bool aligned(const void* p, uintptr_t b) { return ((uintptr_t)p % b) == 0; }
+
+}  // namespace
+
+void build_period_buckets(const std::vector<int32_t>& nu, PeriodBuckets& pb) {
+    const int32_t n = (int32_t)nu.size();
+    pb.host_perm.resize((size_t)n);
+    std::iota(pb.host_perm.begin(), pb.host_perm.end(), 0);
+    std::stable_sort(pb.host_perm.begin(), pb.host_perm.end(),
+                     [&](int32_t x, int32_t y) { return nu[(size_t)x] < nu[(size_t)y]; });
+    pb.period.clear();
+    pb.start.clear();
+    pb.len.clear();
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t v = nu[(size_t)pb.host_perm[(size_t)k]];
+        if (pb.period.empty() || pb.period.back() != v) {
+            pb.period.push_back(v);
+            pb.start.push_back(k);
+            pb.len.push_back(0);
+        }
+        ++pb.len.back();
+    }
+}
+
+bool variant_words_ok(const StepArgs& a) {
+    return a.T % 128 == 0 && (int64_t)a.n * (a.T / 128) < (1ll << 31) && aligned(a.in, 4) && aligned(a.out, 4) &&
+           (a.alg != 1 || aligned(a.Iprev, 16)) && (a.alg != 2 || aligned(a.ring, 8));
+}
+
+cudaError_t launch_variant_step(const StepArgs& base, const PeriodBuckets* pb, cudaStream_t s, SparseVariant v) {
+    if (!variant_words_ok(base)) {
+        StepArgs a = base;
+        a.carry = 0;  // the group tile copies every idle node
+        return launch_sparse_step(a, s, v);
+    }
+    VariantLaunch L{};
+    L.a = base;
+    // words per lane: up to two (PBIT_VARIANT_NW sets the cap, 1, 2 or 4).  Measured on GB300, 100x200
+    // torus, T = 1024, µs per step with one, two and four words: SpSA 96 / 84 / 88, TApSA 112 / 101 / 111,
+    // timing model (t_res = 10) 14.0 / 12.7 / 13.3 per sub-step.
+    static const int nw_cap = std::getenv("PBIT_VARIANT_NW") ? std::atoi(std::getenv("PBIT_VARIANT_NW")) : 2;
+    const int NW = base.T % 512 == 0 && nw_cap >= 4 ? 4 : (base.T % 256 == 0 && nw_cap >= 2 ? 2 : 1);
+    L.spans = (uint32_t)(base.T / (128 * NW));
+    magic_divisor(L.spans, L.span_m, L.span_s);
+    L.nranges = 0;
+    L.warps = (uint32_t)((int64_t)base.n * L.spans);
+    if (base.t_res > 0 && base.carry && pb && pb->perm && !pb->period.empty()) {
+        // nodes due at q or q - 1, as runs of the period-sorted permutation
+        const uint32_t q = (uint32_t)base.step;
+        int nr = 0;
+        uint32_t warps = 0;
+        int32_t run_end = -1;
+        bool fits = true;
+        for (size_t b = 0; b < pb->period.size(); ++b) {
+            const uint32_t p = (uint32_t)pb->period[b];
+            if (q % p != 0u && (q - 1u) % p != 0u) continue;
+            if (pb->start[b] == run_end) {
+                L.rwarp_end[nr - 1] += (uint32_t)pb->len[b] * L.spans;
+            } else {
+                if (nr == kMaxRanges) {
+                    fits = false;
+                    break;
+                }
+                L.rstart[nr] = pb->start[b];
+                L.rwarp_end[nr] = warps + (uint32_t)pb->len[b] * L.spans;
+                ++nr;
+            }
+            warps += (uint32_t)pb->len[b] * L.spans;
+            run_end = pb->start[b] + pb->len[b];
+        }
+        if (fits) {
+            L.a.perm = pb->perm;
+            L.nranges = nr;
+            L.warps = warps;
+            if (nr == 0) return cudaSuccess;  // nothing due now or a sub-step ago: both buffers agree
+        }
+    }
+    if (NW == 4) return v.unit ? launch_words<4, true>(L, s) : launch_words<4, false>(L, s);
+    if (NW == 2) return v.unit ? launch_words<2, true>(L, s) : launch_words<2, false>(L, s);
+    return v.unit ? launch_words<1, true>(L, s) : launch_words<1, false>(L, s);
+}
+
+}  // namespace pbit

@@ -23,8 +23,12 @@ def _host(t):
     return t.cpu().numpy()
 
 
-def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mode=pbit.OFFSET_SCALED):
+def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mode=pbit.OFFSET_SCALED,
+              int_weights=False):
     g = inputs.erdos_renyi_gnm(500, 2500, 3, "pm1")
+    if int_weights:  # weights in [-3, 3] \ {0}: the general (non +-1) field gather
+        w = np.random.default_rng(9).integers(1, 4, g.m) * np.where(np.random.default_rng(10).random(g.m) < 0.5, -1, 1)
+        g.w = w.astype(np.int8)
     var = inputs.variability(g.n, 3, s_intensity=0.3, s_offset=0.3)
     G = pbit.Graph.from_inputs(g)
     csr = oracle.Csr(g.n, g.src, g.dst, g.w)
@@ -80,13 +84,65 @@ def test_timing_model_lockstep():
     assert _lockstep(pbit.ALG_TAPSA, steps=25, t_res=10, nu_dev=nu) <= 2
 
 
+@pytest.mark.parametrize("T", [128, 256, 1024])
+@pytest.mark.parametrize("int_weights", [False, True])
+def test_word_tile_lockstep(T, int_weights):
+    """T a multiple of 128: the coalesced word tile (one, two or four words per lane), +-1 and integer weights."""
+    nu = np.random.default_rng(2).normal(0, 0.5, 500).astype(np.float32)
+    assert _lockstep(pbit.ALG_SPSA, T=T, steps=6, int_weights=int_weights) <= 2
+    assert _lockstep(pbit.ALG_TAPSA, T=T, steps=6, int_weights=int_weights) <= 2
+    assert _lockstep(pbit.ALG_PSA, T=T, steps=12, t_res=10, nu_dev=nu, int_weights=int_weights) <= 2
+
+
+@pytest.mark.parametrize("T", [128, 1024, 96])
+@pytest.mark.parametrize("alg", [pbit.ALG_PSA, pbit.ALG_SPSA, pbit.ALG_TAPSA])
+def test_timing_model_one_call_equals_sub_step_calls(T, alg):
+    """One call over many sub-steps (idle nodes copied only when the output buffer lacks them, warps launched
+    for the nodes due at q or q - 1 alone) equals one call per sub-step (every idle node copied)."""
+    g = inputs.torus_2d(20, 30, 2, "pm1")
+    nu = np.random.default_rng(3).normal(0, 0.15, g.n).astype(np.float32)
+    G = pbit.Graph.from_inputs(g)
+    S, t_res, Q = 6, 10, 47
+    kw = dict(seed=7, algorithm=alg, t_res=t_res, nu_dev=nu, window=3)
+    nbytes = pbit.pbit_variant_state_bytes(g.n, T, alg, 3)
+    st1 = torch.zeros(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    st2 = torch.zeros_like(st1)
+    s0 = _dev(oracle.init_spins(g.n, T, 7))
+    one = torch.empty_like(s0)
+    p, keep = pbit.make_params(T, S, step_end=Q, state=st1 if nbytes else None, **kw)
+    l0 = pbit.pbit_launch_count()
+    pbit.pbit_anneal(G.handle, p, s0, one)
+    launches = pbit.pbit_launch_count() - l0
+    cur = s0.clone()
+    for q in range(Q):
+        nxt = torch.empty_like(cur)
+        p, keep = pbit.make_params(T, S, step_begin=q, step_end=q + 1, state=st2 if nbytes else None, **kw)
+        pbit.pbit_anneal(G.handle, p, cur, nxt)
+        cur = nxt
+    assert np.array_equal(_host(one), _host(cur))
+    if nbytes:
+        assert torch.equal(st1, st2)
+    assert launches <= Q
+
+
+def test_tapsa_rejects_fields_beyond_int16():
+    g = inputs.complete_pm1(300, 1)
+    h = np.full(g.n, 32767 - 200, np.int32)
+    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h)
+    with pytest.raises(pbit.PbitError) as ei:
+        G.anneal(16, 10, algorithm=pbit.ALG_TAPSA)
+    assert ei.value.code == pbit.PBIT_E_UNSUPPORTED
+    G.anneal(16, 10, algorithm=pbit.ALG_SPSA)
+
+
 def test_variants_in_batch_equal_alone():
     gs = [inputs.erdos_renyi_gnm(700, 2100, 1, "+1"), inputs.rgg_knn(900, 2, 3, "pm1"),
-          inputs.torus_2d(20, 25, 3, "pm1")]
+          inputs.torus_2d(20, 25, 3, "pm1"), inputs.torus_2d(20, 25, 4, "pm1")]
     nu = np.random.default_rng(5).normal(0, 0.3, 900).astype(np.float32)
     kws = [dict(trials=64, steps=50, seed=1, algorithm=pbit.ALG_SPSA),
            dict(trials=48, steps=40, seed=2, algorithm=pbit.ALG_TAPSA, window=4),
-           dict(trials=32, steps=6, seed=3, t_res=10, nu_dev=nu[:500], algorithm=pbit.ALG_PSA)]
+           dict(trials=128, steps=6, seed=3, t_res=10, nu_dev=nu[:500], algorithm=pbit.ALG_TAPSA),
+           dict(trials=32, steps=6, seed=4, t_res=10, nu_dev=nu[:500], algorithm=pbit.ALG_PSA)]
     Gs = [pbit.Graph.from_inputs(g) for g in gs]
     B = pbit.Batch(Gs, kws)
     B.run(chunk_steps=16)
