@@ -123,8 +123,8 @@ def variant_work(variant: dict, g, T: int, Q: int):
     An update of node i reads deg_i neighbour bytes and its own, writes one, and carries its state
     (SpSA: the float32 input read and written, 8 B; TApSA: window - 1 int16 fields read, one written,
     2 window B).  Timing model (period nu_i = max(1, round(t_res (1 + nu_dev_i)))): node i updates at
-    the sub-steps q % nu_i == 0 only; an idle node copies its spin (2 B) where the output buffer lacks
-    it: at sub-step 1, and at every later sub-step right after one of its updates."""
+    the sub-steps q % nu_i == 0 only and an idle node costs nothing (the parity form copies no spins
+    between sub-steps; its two placement passes per call are not counted)."""
     from paper_2601_14476_gb300 import pbit
     alg = variant.get("algorithm", pbit.ALG_PSA)
     state = 8 if alg == pbit.ALG_SPSA else (2 * variant.get("window", 4) if alg == pbit.ALG_TAPSA else 0)
@@ -135,8 +135,7 @@ def variant_work(variant: dict, g, T: int, Q: int):
     dev = np.zeros(g.n) if variant.get("nu_dev") is None else np.asarray(variant["nu_dev"], np.float32)
     nu = np.maximum(1, np.floor(t_res * (1.0 + dev.astype(np.float64)) + 0.5)).astype(np.int64)
     due = (Q + nu - 1) // nu
-    copies = np.where(nu > 1, (1 + (Q - 2) // nu) if Q >= 2 else 0, 0)
-    return T * int(due.sum()), T * float((due * (deg + 2 + state)).sum() + 2 * copies.sum())
+    return T * int(due.sum()), T * float((due * (deg + 2 + state)).sum())
 
 
 def workload_config(w) -> dict:
@@ -650,7 +649,7 @@ def main():
                     "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,
                     "kernel": kname,
                     "peak_source": pk["source"],
-                    "per_launch": (f"variant bytes of the whole run (deg+2+state per update, 2 per copy) / "
+                    "per_launch": (f"variant bytes of the whole run (deg+2+state per update) / "
                                    f"{launches_main} launches" if variant else
                                    f"(deg+2) bytes x n*T updates per step; {launches_main} launches")}
     roofline["kernel_ms_per_anneal"] = anneal_ms

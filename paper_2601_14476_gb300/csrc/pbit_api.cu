@@ -583,6 +583,13 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         int32_t* dp = nullptr;
         if ((st = cb.put(&dp, buckets.host_perm.data(), buckets.host_perm.size())) != PBIT_OK) return st;
         buckets.perm = dp;
+        if (!buckets.host_bkt.empty()) {
+            uint8_t* db = nullptr;
+            if ((st = cb.put(&db, buckets.host_bkt.data(), buckets.host_bkt.size())) != PBIT_OK) return st;
+            buckets.bkt = db;
+            if ((st = cb.alloc(&buckets.ebkt, (size_t)g->nnz)) != PBIT_OK) return st;
+            PBIT_CUDA_TRY(launch_edge_buckets(*g, buckets.bkt, buckets.ebkt, s));
+        }
     }
     if (a.alg != PBIT_ALG_PSA) {
         const size_t sb = pbit_variant_state_bytes(g->n, T, a.alg, a.window);
@@ -648,6 +655,16 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         PBIT_CUDA_TRY(launch_from_tiled(*g, t0, T, spins_out, s));
         return PBIT_OK;
     }
+    const SparseVariant variant = choose_sparse_variant(*g, T);
+    static const bool timing_copy = std::getenv("PBIT_TIMING_COPY") != nullptr;  // force the copy form (tests)
+    if (a.t_res > 0 && buckets.ebkt && !timing_copy) {
+        // timing model, parity form: each node's spins alternate between spins_out and a scratch buffer
+        int8_t* other = nullptr;
+        if ((st = cb.alloc(&other, (size_t)cells)) != PBIT_OK) return st;
+        const cudaError_t te = launch_timing_slots(*g, a, b, e, cur, spins_out, other, buckets, variant, s);
+        if (te == cudaSuccess) return PBIT_OK;
+        if (te != cudaErrorNotSupported) return cuda_fail(te, "timing model");
+    }
     // Jacobi rotation: step j writes spins_out when (k-1-j) is even, else scratch
     int8_t* scratch = nullptr;
     const int32_t k = e - b;
@@ -659,7 +676,6 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         PBIT_CUDA_TRY(cudaMemcpyAsync(scratch, cur, (size_t)cells, cudaMemcpyDeviceToDevice, s));
         cur = scratch;
     }
-    const SparseVariant variant = choose_sparse_variant(*g, T);
     // plain pSA over two or more steps: one persistent launch with per-tile step dependencies
     static const bool stepwise = std::getenv("PBIT_SPARSE_STEPWISE") != nullptr;  // force one launch per step
     // PBIT_SPARSE_FLOW=always takes the multi-step form whatever the dependency structure (tests)

@@ -161,11 +161,19 @@ __host__ __device__ inline bool is_variant(const StepArgs& a) { return a.alg != 
 // period so that a sub-step with `carry` launches warps only for the nodes due at q or q - 1.
 struct PeriodBuckets {
     const int32_t* perm = nullptr;             // device [n]: node ids sorted by period
+    const uint8_t* bkt = nullptr;              // device [n]: bucket of each node (at most 32 buckets)
+    uint8_t* ebkt = nullptr;                   // device [nnz]: bucket of each edge's column
     std::vector<int32_t> host_perm;
-    std::vector<int32_t> period, start, len;   // per distinct period: its run [start, start + len) of perm
+    std::vector<uint8_t> host_bkt;             // empty when there are more than 32 periods
+    std::vector<int32_t> period, start, len;   // per distinct period (ascending): its run [start, start + len) of perm
 };
 void build_period_buckets(const std::vector<int32_t>& nu, PeriodBuckets& pb);
+cudaError_t launch_edge_buckets(const Graph& g, const uint8_t* bkt, uint8_t* ebkt, cudaStream_t s);
 cudaError_t launch_variant_step(const StepArgs& a, const PeriodBuckets* pb, cudaStream_t s, SparseVariant v);
+// Sub-steps [b, e) of the timing model in the parity form (pbit_variant.cu): the result lands in X; Y is
+// scratch of n*T bytes; cur may be X.  cudaErrorNotSupported when the form does not apply.
+cudaError_t launch_timing_slots(const Graph& g, const StepArgs& a, int32_t b, int32_t e, const int8_t* cur, int8_t* X,
+                                int8_t* Y, const PeriodBuckets& pb, SparseVariant v, cudaStream_t s);
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s);
 cudaError_t launch_cut_energy(const Graph& g, const int8_t* spins, int32_t T, int64_t* out, bool energy,
                               cudaStream_t s);

@@ -10,13 +10,20 @@
 // fields per ring slot.  The state keeps its plain [n][T] (SpSA) and
 // [window][n][T] (TApSA) layout.
 //
-// Timing model: a node that is not due copies its spins to the output buffer,
-// but only when that buffer does not already hold them.  In the Jacobi
-// rotation the output of sub-step q holds the state of sub-step q - 2
-// (`carry`), which differs from the state of q - 1 only for the nodes due at
-// q - 1, so with `carry` a sub-step touches the nodes due at q or q - 1 only.
-// The host groups the nodes by period (PeriodBuckets) and launches warps for
-// those two groups of periods alone.
+// Timing model, two forms.  Parity form (used when the nodes take at most 32
+// distinct periods): node i has updated K_i(q) = ceil(q / nu_i) times before
+// sub-step q, and its spins live in spins_out when K_i(q) is odd and in the
+// scratch buffer when it is even.  A due node reads its spins and its
+// neighbours' from where their counts put them and writes the other buffer;
+// no neighbour writes a buffer it reads, so the update stays synchronous, and
+// a sub-step launches warps for its due nodes alone (the host groups the
+// nodes by period and passes the runs of due periods and the parity of every
+// period).  One pass at the start places the input by parity, one at the end
+// gathers the result into spins_out.  Copy form (otherwise): the Jacobi
+// rotation, where a node that is not due copies its spins to the output
+// buffer, but only when that buffer lacks them: the output of sub-step q holds
+// the state of q - 2 (`carry`), which differs from that of q - 1 only for the
+// nodes due at q - 1.
 #include "pbit_internal.h"
 #include "pbit_device.cuh"
 #include "pbit_tile.cuh"
@@ -36,6 +43,11 @@ constexpr int kMaxRanges = 32;
 
 struct VariantLaunch {
     StepArgs a;
+    int32_t slots;            // parity form: a.out holds odd update counts, alt even ones
+    int8_t* alt;
+    const uint8_t* bkt;       // [n] period bucket of each node
+    const uint8_t* ebkt;      // [nnz] period bucket of each edge's column
+    uint32_t pmask;           // bit b: ceil(q / period_b) & 1
     uint32_t spans;           // spans per node: T / (128 * NW)
     uint64_t span_m;          // local warp -> node: (w * span_m) >> span_s = w / spans
     int32_t span_s;
@@ -78,7 +90,19 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
     const uint32_t q = (uint32_t)a.step;
     const int tb = (int)sidx * (128 * NW) + 4 * lane;  // trial of word 0; word k at tb + 128 k
     const size_t row = (size_t)i * T;
-    if (a.t_res > 0) {
+    // where the node's spins are read and written, and where neighbour j's are read
+    const int8_t* src = a.in;
+    int8_t* dst = a.out;
+    if (L.slots) {
+        const bool odd = (L.pmask >> __ldg(L.bkt + i)) & 1u;
+        src = odd ? a.out : L.alt;
+        dst = odd ? L.alt : a.out;
+    }
+    const auto nbr = [&](int e) -> const int8_t* {
+        if (!L.slots) return a.in;
+        return ((L.pmask >> __ldg(L.ebkt + e)) & 1u) ? a.out : L.alt;
+    };
+    if (a.t_res > 0 && !L.slots) {
         const uint32_t nu = (uint32_t)__ldg(a.nu + i);
         if (q % nu != 0u) {
             if (!a.carry || (q - 1u) % nu == 0u) {
@@ -131,7 +155,7 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
 #pragma unroll
         for (int k = 0; k < NW; ++k) cnt2[k] = 0;
         for (int e = rb; e < re; ++e) {
-            const int8_t* pj = a.in + (size_t)__ldg(a.col + e) * T + tb;
+            const int8_t* pj = nbr(e) + (size_t)__ldg(a.col + e) * T + tb;
             const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
 #pragma unroll
             for (int k = 0; k < NW; ++k) cnt2[k] += (ld32(pj + 128 * k) & 0x02020202u) ^ flip;
@@ -145,7 +169,7 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
 #pragma unroll
         for (int k = 0; k < 4 * NW; ++k) D[k] = hi;
         for (int e = rb; e < re; ++e) {
-            const int8_t* pj = a.in + (size_t)__ldg(a.col + e) * T + tb;
+            const int8_t* pj = nbr(e) + (size_t)__ldg(a.col + e) * T + tb;
             const int w = __ldg(a.J + e);
 #pragma unroll
             for (int k = 0; k < NW; ++k) {
@@ -196,9 +220,28 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
         const uint32_t k3 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[3]));
         const uint32_t S = sign_bytes((r0.x >> 8) - k0, (r0.z >> 8) - k1, (r1.x >> 8) - k2, (r1.z >> 8) - k3);
         const uint32_t U = sign_bytes((r0.y >> 8) - thr, (r0.w >> 8) - thr, (r1.y >> 8) - thr, (r1.w >> 8) - thr);
-        const uint32_t old = ld32(a.in + cell);
-        st32(a.out + cell, ((U & ~S) | (~U & old)) | 0x01010101u);
+        const uint32_t old = ld32(src + cell);
+        st32(dst + cell, ((U & ~S) | (~U & old)) | 0x01010101u);
     }
+}
+
+// Parity form, start and end: node i's row moves from src[P] to dst[P], P the parity of its count.
+__global__ void slot_move_kernel(int32_t n, int32_t words, const uint8_t* __restrict__ bkt, uint32_t pmask,
+                                 const int8_t* src0, const int8_t* src1, int8_t* dst0, int8_t* dst1) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= (int64_t)n * words) return;
+    const int i = (int)(k / words);
+    const bool odd = (pmask >> __ldg(bkt + i)) & 1u;
+    const int8_t* sp = odd ? src1 : src0;
+    int8_t* dp = odd ? dst1 : dst0;
+    if ((const void*)sp == (const void*)dp) return;
+    reinterpret_cast<uint32_t*>(dp)[k] = reinterpret_cast<const uint32_t*>(sp)[k];
+}
+
+__global__ void edge_bucket_kernel(int64_t nnz, const int32_t* __restrict__ col, const uint8_t* __restrict__ bkt,
+                                   uint8_t* __restrict__ ebkt) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < nnz) ebkt[e] = __ldg(bkt + __ldg(col + e));
 }
 
 template <int NW, bool UNIT>
@@ -235,11 +278,112 @@ void build_period_buckets(const std::vector<int32_t>& nu, PeriodBuckets& pb) {
         }
         ++pb.len.back();
     }
+    pb.host_bkt.clear();
+    if (pb.period.size() <= 32) {
+        pb.host_bkt.resize((size_t)n);
+        for (size_t b = 0; b < pb.period.size(); ++b)
+            for (int32_t k = pb.start[b]; k < pb.start[b] + pb.len[b]; ++k) pb.host_bkt[(size_t)pb.host_perm[(size_t)k]] = (uint8_t)b;
+    }
+}
+
+cudaError_t launch_edge_buckets(const Graph& g, const uint8_t* bkt, uint8_t* ebkt, cudaStream_t s) {
+    if (g.nnz == 0) return cudaSuccess;
+    edge_bucket_kernel<<<(unsigned)((g.nnz + 255) / 256), 256, 0, s>>>(g.nnz, g.col, bkt, ebkt);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 bool variant_words_ok(const StepArgs& a) {
     return a.T % 128 == 0 && (int64_t)a.n * (a.T / 128) < (1ll << 31) && aligned(a.in, 4) && aligned(a.out, 4) &&
            (a.alg != 1 || aligned(a.Iprev, 16)) && (a.alg != 2 || aligned(a.ring, 8));
+}
+
+namespace {
+
+// Words per lane and the warp -> node divisor for the word tile.
+void words_config(VariantLaunch& L) {
+    // words per lane: up to two (PBIT_VARIANT_NW sets the cap, 1, 2 or 4).  Measured on GB300, 100x200
+    // torus, T = 1024, µs per step with one, two and four words: SpSA 96 / 84 / 88, TApSA 112 / 101 / 111,
+    // timing model (t_res = 10, copy form) 14.0 / 12.7 / 13.3 per sub-step.
+    static const int nw_cap = std::getenv("PBIT_VARIANT_NW") ? std::atoi(std::getenv("PBIT_VARIANT_NW")) : 2;
+    const int T = L.a.T;
+    const int NW = T % 512 == 0 && nw_cap >= 4 ? 4 : (T % 256 == 0 && nw_cap >= 2 ? 2 : 1);
+    L.spans = (uint32_t)(T / (128 * NW));
+    magic_divisor(L.spans, L.span_m, L.span_s);
+    L.nranges = 0;
+    L.warps = (uint32_t)((int64_t)L.a.n * L.spans);
+}
+
+cudaError_t launch_words_any(const VariantLaunch& L, SparseVariant v, cudaStream_t s) {
+    const int NW = (int)(L.a.T / (128 * L.spans));
+    if (NW == 4) return v.unit ? launch_words<4, true>(L, s) : launch_words<4, false>(L, s);
+    if (NW == 2) return v.unit ? launch_words<2, true>(L, s) : launch_words<2, false>(L, s);
+    return v.unit ? launch_words<1, true>(L, s) : launch_words<1, false>(L, s);
+}
+
+cudaError_t launch_move(const Graph& g, int32_t T, const uint8_t* bkt, uint32_t pmask, const int8_t* src0,
+                        const int8_t* src1, int8_t* dst0, int8_t* dst1, cudaStream_t s) {
+    const int64_t total = (int64_t)g.n * (T / 4);
+    if (total == 0) return cudaSuccess;
+    slot_move_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g.n, T / 4, bkt, pmask, src0, src1, dst0, dst1);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+uint32_t parity_mask(const PeriodBuckets& pb, uint32_t q) {
+    uint32_t m = 0;
+    for (size_t b = 0; b < pb.period.size(); ++b) {
+        const uint32_t p = (uint32_t)pb.period[b];
+        m |= (((q + p - 1u) / p) & 1u) << b;
+    }
+    return m;
+}
+
+}  // namespace
+
+cudaError_t launch_timing_slots(const Graph& g, const StepArgs& base, int32_t b, int32_t e, const int8_t* cur,
+                                int8_t* X, int8_t* Y, const PeriodBuckets& pb, SparseVariant v, cudaStream_t s) {
+    VariantLaunch L{};
+    L.a = base;
+    L.a.in = X;
+    L.a.out = X;
+    if (base.t_res <= 0 || !variant_words_ok(L.a) || !aligned(Y, 4) || !aligned(cur, 4) || pb.period.empty() ||
+        pb.period.size() > 32 || !pb.bkt || !pb.ebkt || !pb.perm || (int64_t)e + pb.period.back() >= (1ll << 31))
+        return cudaErrorNotSupported;
+    words_config(L);
+    L.slots = 1;
+    L.alt = Y;
+    L.bkt = pb.bkt;
+    L.ebkt = pb.ebkt;
+    L.a.perm = pb.perm;
+    const int32_t T = base.T;
+    cudaError_t err = launch_move(g, T, pb.bkt, parity_mask(pb, (uint32_t)b), cur, cur, Y, X, s);
+    if (err != cudaSuccess) return err;
+    for (int32_t q = b; q < e; ++q) {
+        // the due nodes, as runs of the period-sorted permutation
+        int nr = 0;
+        uint32_t warps = 0;
+        int32_t run_end = -1;
+        for (size_t k = 0; k < pb.period.size(); ++k) {
+            if ((uint32_t)q % (uint32_t)pb.period[k] != 0u) continue;
+            if (pb.start[k] == run_end) {
+                L.rwarp_end[nr - 1] += (uint32_t)pb.len[k] * L.spans;
+            } else {
+                L.rstart[nr] = pb.start[k];
+                L.rwarp_end[nr] = warps + (uint32_t)pb.len[k] * L.spans;
+                ++nr;
+            }
+            warps += (uint32_t)pb.len[k] * L.spans;
+            run_end = pb.start[k] + pb.len[k];
+        }
+        if (nr == 0) continue;
+        L.a.step = q;
+        L.nranges = nr;
+        L.warps = warps;
+        L.pmask = parity_mask(pb, (uint32_t)q);
+        if ((err = launch_words_any(L, v, s)) != cudaSuccess) return err;
+    }
+    return launch_move(g, T, pb.bkt, parity_mask(pb, (uint32_t)e), Y, X, X, X, s);
 }
 
 cudaError_t launch_variant_step(const StepArgs& base, const PeriodBuckets* pb, cudaStream_t s, SparseVariant v) {
@@ -250,15 +394,7 @@ cudaError_t launch_variant_step(const StepArgs& base, const PeriodBuckets* pb, c
     }
     VariantLaunch L{};
     L.a = base;
-    // words per lane: up to two (PBIT_VARIANT_NW sets the cap, 1, 2 or 4).  Measured on GB300, 100x200
-    // torus, T = 1024, µs per step with one, two and four words: SpSA 96 / 84 / 88, TApSA 112 / 101 / 111,
-    // timing model (t_res = 10) 14.0 / 12.7 / 13.3 per sub-step.
-    static const int nw_cap = std::getenv("PBIT_VARIANT_NW") ? std::atoi(std::getenv("PBIT_VARIANT_NW")) : 2;
-    const int NW = base.T % 512 == 0 && nw_cap >= 4 ? 4 : (base.T % 256 == 0 && nw_cap >= 2 ? 2 : 1);
-    L.spans = (uint32_t)(base.T / (128 * NW));
-    magic_divisor(L.spans, L.span_m, L.span_s);
-    L.nranges = 0;
-    L.warps = (uint32_t)((int64_t)base.n * L.spans);
+    words_config(L);
     if (base.t_res > 0 && base.carry && pb && pb->perm && !pb->period.empty()) {
         // nodes due at q or q - 1, as runs of the period-sorted permutation
         const uint32_t q = (uint32_t)base.step;
@@ -290,9 +426,7 @@ cudaError_t launch_variant_step(const StepArgs& base, const PeriodBuckets* pb, c
             if (nr == 0) return cudaSuccess;  // nothing due now or a sub-step ago: both buffers agree
         }
     }
-    if (NW == 4) return v.unit ? launch_words<4, true>(L, s) : launch_words<4, false>(L, s);
-    if (NW == 2) return v.unit ? launch_words<2, true>(L, s) : launch_words<2, false>(L, s);
-    return v.unit ? launch_words<1, true>(L, s) : launch_words<1, false>(L, s);
+    return launch_words_any(L, v, s);
 }
 
 }  // namespace pbit

@@ -94,13 +94,15 @@ def test_word_tile_lockstep(T, int_weights):
     assert _lockstep(pbit.ALG_PSA, T=T, steps=12, t_res=10, nu_dev=nu, int_weights=int_weights) <= 2
 
 
-@pytest.mark.parametrize("T", [128, 1024, 96])
+@pytest.mark.parametrize("T,spread", [(128, 0.15), (1024, 0.15), (96, 0.15), (256, 3.0)])
 @pytest.mark.parametrize("alg", [pbit.ALG_PSA, pbit.ALG_SPSA, pbit.ALG_TAPSA])
-def test_timing_model_one_call_equals_sub_step_calls(T, alg):
-    """One call over many sub-steps (idle nodes copied only when the output buffer lacks them, warps launched
-    for the nodes due at q or q - 1 alone) equals one call per sub-step (every idle node copied)."""
+def test_timing_model_one_call_equals_sub_step_calls(T, spread, alg):
+    """One call over many sub-steps equals one call per sub-step.  T = 128, 1024: the parity form (spins
+    alternate between two buffers by update count; warps for the due nodes only); T = 96: the copy form
+    (idle nodes copied where the output buffer lacks them); spread 3.0: more than 32 distinct periods,
+    so the copy form on the word tile."""
     g = inputs.torus_2d(20, 30, 2, "pm1")
-    nu = np.random.default_rng(3).normal(0, 0.15, g.n).astype(np.float32)
+    nu = np.random.default_rng(3).normal(0, spread, g.n).astype(np.float32)
     G = pbit.Graph.from_inputs(g)
     S, t_res, Q = 6, 10, 47
     kw = dict(seed=7, algorithm=alg, t_res=t_res, nu_dev=nu, window=3)
@@ -122,7 +124,30 @@ def test_timing_model_one_call_equals_sub_step_calls(T, alg):
     assert np.array_equal(_host(one), _host(cur))
     if nbytes:
         assert torch.equal(st1, st2)
-    assert launches <= Q
+    assert launches <= Q + 3
+
+
+@pytest.mark.parametrize("alg", [pbit.ALG_PSA, pbit.ALG_TAPSA])
+def test_timing_model_parity_form_equals_copy_form(tmp_path, alg):
+    """The parity form and the copy form (forced in a child process) give the same anneal, T = 1024."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2601_14476_gb300 import inputs, pbit\n"
+        "g = inputs.torus_2d(30, 40, 5, 'pm1')\n"
+        "nu = inputs.timing_deviation(g.n, 5, 0.1)\n"
+        "G = pbit.Graph.from_inputs(g)\n"
+        f"out = G.anneal(1024, 40, seed=6, algorithm={alg}, t_res=10, nu_dev=nu, variability=inputs.variability(g.n, 5))\n"
+        "torch.cuda.synchronize(); G.status()\n"
+        "np.save(%r, out.cpu().numpy())\n")
+    outs = []
+    for k, env_extra in enumerate(({}, {"PBIT_TIMING_COPY": "1"})):
+        path = str(tmp_path / f"o{k}.npy")
+        subprocess.run([sys.executable, "-c", code % path], check=True, env=dict(os.environ, **env_extra), timeout=300)
+        outs.append(np.load(path))
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_tapsa_rejects_fields_beyond_int16():
