@@ -40,6 +40,15 @@ TRAFFIC = {
     "sparse_flow_kernel": {"bytes": 23335680 + 5099264,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
                            "sha": "5fedf916d58b284d", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
+    # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
+    "sparse_variant_words_kernel:spsa": {"bytes": 103567189 + 41314645,
+                                         "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
+                                         "sha": "d5731523a7973f95",
+                                         "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
+    "sparse_variant_words_kernel:tapsa": {"bytes": 144540245 + 35561813,
+                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
+                                          "sha": "d5731523a7973f95",
+                                          "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
     # per launch of a 64-step chunk of all 64 instances
     "batch_chunk_kernel": {"bytes": 811351552 + 1346066432, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
                            "sha": "90f3bf29cc6398a2", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
@@ -75,9 +84,9 @@ def sparse_tile_kernel(g, T: int, launches_per_anneal: float, steps: int) -> str
     return "sparse_step_kernel"
 
 
-def traffic_for(kernel: str):
+def traffic_for(kernel):
     import hashlib
-    t = TRAFFIC.get(kernel)
+    t = TRAFFIC.get(kernel) if kernel else None
     if not t:
         return None
     m = hashlib.sha256()
@@ -136,6 +145,16 @@ def variant_work(variant: dict, g, T: int, Q: int):
     nu = np.maximum(1, np.floor(t_res * (1.0 + dev.astype(np.float64)) + 0.5)).astype(np.int64)
     due = (Q + nu - 1) // nu
     return T * int(due.sum()), T * float((due * (deg + 2 + state)).sum())
+
+
+def traffic_key(kname: str, variant: dict):
+    """TRAFFIC entry of a launch: per kernel; the variants' one-step launches per algorithm (the timing
+    model's launches vary in size with the due nodes, so they have none)."""
+    if not variant:
+        return kname
+    if variant.get("t_res", 0) > 0 or variant.get("algorithm", 0) not in (1, 2) or variant.get("window", 4) != 4:
+        return None
+    return f"{kname}:{'spsa' if variant['algorithm'] == 1 else 'tapsa'}"
 
 
 def workload_config(w) -> dict:
@@ -646,7 +665,7 @@ def main():
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"],
-                    "traffic": traffic_for(kname) if g.n == 20000 and T == 1024 else None,
+                    "traffic": traffic_for(traffic_key(kname, variant)) if g.n == 20000 and T == 1024 else None,
                     "kernel": kname,
                     "peak_source": pk["source"],
                     "per_launch": (f"variant bytes of the whole run (deg+2+state per update) / "

@@ -70,7 +70,7 @@ __device__ __forceinline__ void st32(int8_t* p, uint32_t v) { *reinterpret_cast<
 
 // WIN: the TApSA window when it is 4 (the paper's; its other-slot loads unrolled), else 0
 template <int NW, bool UNIT, int WIN>
-__global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __grid_constant__ VariantLaunch L) {
+__global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words_kernel(const __grid_constant__ VariantLaunch L) {
     const StepArgs& a = L.a;
     const uint32_t warp = (blockIdx.x * (uint32_t)kVBlock + threadIdx.x) >> 5;
     const int lane = (int)(threadIdx.x & 31u);
@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
     }
     // exact fields D = h_i + sum_j J_ij s_j (Eq. 1)
     int D[4 * NW];
+    uint32_t cnt2[NW];  // +-1 weights: per trial byte, 2 per neighbour with J_ij s_j = -1
     if constexpr (UNIT) {
-        // +-1 weights: count 2 per neighbour with J_ij s_j = -1 (bit 1 of the spin byte, flipped for J = -1)
-        uint32_t cnt2[NW];
+        // bit 1 of the spin byte is set for -1; flipped for J = -1
 #pragma unroll
         for (int k = 0; k < NW; ++k) cnt2[k] = 0;
         for (int e = rb; e < re; ++e) {
@@ -177,6 +177,18 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
 #pragma unroll
                 for (int b = 0; b < 4; ++b) D[4 * k + b] += w * tile::sbyte(v, b);
             }
+        }
+    }
+    // pSA under the timing model with +-1 weights and degree <= 15: the input depends on the count
+    // alone, so lane c (every lane of the warp has node i) computes the threshold of count c once and
+    // each trial reads its own with a shuffle; the same float operations as the per-trial form
+    bool table = false;
+    uint32_t negk_lane = 0;
+    if constexpr (UNIT) {
+        if (a.alg == 0 && 2 * (re - rb) + 1 <= 32) {
+            table = true;
+            const float Ic = __fmul_rn(I0, (float)(hi + (re - rb) - lane));  // counts above 2 deg are never read
+            negk_lane = 0u - pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, Ic));
         }
     }
 #pragma unroll
@@ -214,11 +226,15 @@ __global__ void __launch_bounds__(kVBlock) sparse_variant_words_kernel(const __g
         uint4 r0, r1;
         philox_pair((uint32_t)i, q, (uint32_t)t >> 1, (uint32_t)(t + 2) >> 1, a.instance, a.seed_lo, a.seed_hi, r0,
                     r1);
-        const uint32_t k0 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[0]));
-        const uint32_t k1 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[1]));
-        const uint32_t k2 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[2]));
-        const uint32_t k3 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[3]));
-        const uint32_t S = sign_bytes((r0.x >> 8) - k0, (r0.z >> 8) - k1, (r1.x >> 8) - k2, (r1.z >> 8) - k3);
+        uint32_t nk[4];
+        if (table) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) nk[b] = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)tile::byte_of(cnt2[k], b));
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) nk[b] = 0u - pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[b]));
+        }
+        const uint32_t S = sign_bytes((r0.x >> 8) + nk[0], (r0.z >> 8) + nk[1], (r1.x >> 8) + nk[2], (r1.z >> 8) + nk[3]);
         const uint32_t U = sign_bytes((r0.y >> 8) - thr, (r0.w >> 8) - thr, (r1.y >> 8) - thr, (r1.w >> 8) - thr);
         const uint32_t old = ld32(src + cell);
         st32(dst + cell, ((U & ~S) | (~U & old)) | 0x01010101u);
