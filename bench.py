@@ -247,7 +247,7 @@ def _oracle_sample(job):
     import oracle
     kind, k = job
     if _ORACLE_CASE.get("kind") != kind:
-        w = inputs.batch64()[0] if kind == "batch" else workload(kind)
+        w = multi_reference_workload(kind) if kind in ("batch", "sweep") else workload(kind)
         g = w.graph
         csr = oracle.Csr(g.n, g.src, g.dst, g.w)
         _ORACLE_CASE.update(kind=kind, w=w, csr=csr, tab=oracle.schedule(csr, w.c_min, w.c_max, w.steps),
@@ -359,6 +359,23 @@ def job_throughput(dist, units_per_rank: float, ms_local: float, world: int, dev
     return world * units_per_rank / (ms * 1e-3), ms
 
 
+def sweep_workloads(seed: int = 1, steps: int = 1000):
+    """The variability sweep of the Results section on the G81-shaped 100x200 torus (w in {-1,+1}),
+    128 trials: one instance per point of the default grid (its own variability draw and instance
+    number), all run as one batch."""
+    from paper_2601_14476_gb300 import sweep
+    g = inputs.torus_2d(100, 200, seed, "pm1")
+    return [inputs.Workload(f"sweep_point{k}_torus100x200_T128_S{steps}", g, 128, steps, 0.1, 10.0,
+                            sweep.point_variability(g.n, seed * 1000 + k, pt), seed, k)
+            for k, pt in enumerate(sweep.default_grid())]
+
+
+def multi_reference_workload(config: str):
+    """The single instance the oracle times for the multi-instance configs: the first batch instance
+    (batch, serve: requests come from the same generators) or the sweep point with all three spreads."""
+    return sweep_workloads()[-1] if config == "sweep" else inputs.batch64()[0]
+
+
 def bench_multi(args):
     """config batch: 64 uneven instances, batched persistent form vs plain one-instance-per-launch form.
     config serve: Poisson request stream through the continuous-batching server, p50/p99 latency."""
@@ -367,9 +384,15 @@ def bench_multi(args):
     rank, world, local, dist = _dist_setup()
     pk = peaks()
     stream = torch.cuda.current_stream()
-    if args.config == "batch":
-        ws = inputs.batch64(seed=1 + rank, steps=args.anneal_steps or 2000)
-        Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+    if args.config in ("batch", "sweep"):
+        if args.config == "batch":
+            ws = inputs.batch64(seed=1 + rank, steps=args.anneal_steps or 2000)
+            Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+            wname = f"batch64_uneven_S{ws[0].steps}"
+        else:
+            ws = sweep_workloads(seed=1 + rank, steps=args.anneal_steps or 1000)
+            Gs = [pbit.Graph.from_inputs(ws[0].graph)] * len(ws)
+            wname = f"sweep{len(ws)}_torus100x200_T128_S{ws[0].steps}"
         kws = [dict(trials=w.trials, steps=w.steps, seed=w.seed, instance=w.instance, variability=w.var,
                     i0_min=w.c_min, i0_max=w.c_max) for w in ws]
         upd_run = sum(w.graph.n * w.trials * w.steps for w in ws)
@@ -424,7 +447,8 @@ def bench_multi(args):
         mean_p = float(np.mean([c.mean() for c in plain_cuts]))
         # e2e: graphs from host arrays, batch setup, run, cuts back to host
         t0 = time.perf_counter()
-        G2 = [pbit.Graph.from_inputs(w.graph) for w in ws]
+        G2 = ([pbit.Graph.from_inputs(w.graph) for w in ws] if args.config == "batch"
+              else [pbit.Graph.from_inputs(ws[0].graph)] * len(ws))
         B2 = pbit.Batch(G2, kws)
         pbit.pbit_batch_set_tuning(B2.handle, tuning["chunk_steps"], tuning["ctas_per_sm"])
         B2.run(stream=stream)
@@ -432,14 +456,15 @@ def bench_multi(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         B2.close()
-        h2d = sum(w.graph.m * 9 + (12 * w.graph.n if w.var else 0) + 4 * w.steps for w in ws)
+        h2d = sum((w.graph.m * 9 if (args.config == "batch" or k == 0) else 0) + (12 * w.graph.n if w.var else 0)
+                  + 4 * w.steps for k, w in enumerate(ws))
         d2h = sum(8 * w.trials for w in ws)
         achieved = bytes_run / (ms * 1e-3) / 1e9
         line = {
             "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
-            "config": {"workload": f"batch64_uneven_S{ws[0].steps}", "instances": len(ws),
+            "config": {"workload": wname, "instances": len(ws),
                        "n_range": [min(w.graph.n for w in ws), max(w.graph.n for w in ws)],
                        "trials": sorted(set(w.trials for w in ws)), "updates_per_step": upd_run,
                        "tuning": tuning, "l2": "flushed between timed steps",
@@ -447,7 +472,7 @@ def bench_multi(args):
                        "batched_over_plain": plain_ms / ms, "cuts_identical_to_plain": bool(same),
                        "mean_cut_batched": mean_b, "mean_cut_plain": mean_p},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / pk["hbm_gbs"], "traffic": batch_traffic(tuning, ws[0].steps),
+                         "frac": achieved / pk["hbm_gbs"], "traffic": batch_traffic(tuning, ws[0].steps) if args.config == "batch" else None,
                          "kernel": "batch_chunk_kernel",
                          "peak_source": pk["source"],
                          "per_launch": "sum over instances of (deg+2) bytes x n*T updates per step"},
@@ -457,7 +482,7 @@ def bench_multi(args):
             "gpu_launches": int(launches), "clocks": clk.summary(),
         }
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(ws[0], kind="batch")
+            line["cpu_baseline"] = cpu_baseline(multi_reference_workload(args.config), kind=args.config)
         if rank == 0:
             print(json.dumps(line), flush=True)
         if dist:
@@ -544,7 +569,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain", "batch", "serve"])
+    ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain", "batch", "serve", "sweep"])
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window per rate (serve config)")
     ap.add_argument("--serve-rates", default="10,30,100,300,1000")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -562,7 +587,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.config in ("batch", "serve"):
+    if args.config in ("batch", "serve", "sweep"):
+        if args.impl == "reference":
+            return run_reference(args, multi_reference_workload(args.config))
         return bench_multi(args)
     w = workload(args.config)
     if args.anneal_steps > 0:
