@@ -24,13 +24,14 @@ def _host(t):
 
 
 def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mode=pbit.OFFSET_SCALED,
-              int_weights=False):
+              int_weights=False, bias=False):
     g = inputs.erdos_renyi_gnm(500, 2500, 3, "pm1")
     if int_weights:  # weights in [-3, 3] \ {0}: the general (non +-1) field gather
         w = np.random.default_rng(9).integers(1, 4, g.m) * np.where(np.random.default_rng(10).random(g.m) < 0.5, -1, 1)
         g.w = w.astype(np.int8)
     var = inputs.variability(g.n, 3, s_intensity=0.3, s_offset=0.3)
-    G = pbit.Graph.from_inputs(g)
+    h = np.random.default_rng(11).integers(-6, 7, g.n).astype(np.int32) if bias else None
+    G = pbit.Graph(g.n, g.src, g.dst, g.w, h=h) if bias else pbit.Graph.from_inputs(g)
     csr = oracle.Csr(g.n, g.src, g.dst, g.w)
     S = 8 if t_res else steps
     tab = oracle.schedule(csr, 0.1, 10.0, S)
@@ -53,8 +54,8 @@ def _lockstep(alg, T=32, steps=16, t_res=0, nu_dev=None, window=4, stall=0.5, mo
         pbit.pbit_anneal(G.handle, p, d_in, d_out)
         gpu = _host(d_out)
         want, gap = oracle.step_variant(csr, spins, q, tab, 5, algorithm=alg, stall_prob=stall, window=window,
-                                        t_res=t_res, nu_dev=nu_dev, variability=var, offset_mode=mode, state=ost,
-                                        want_gap=True)
+                                        t_res=t_res, nu_dev=nu_dev, variability=var, h=h, offset_mode=mode,
+                                        state=ost, want_gap=True)
         bad = gpu != want
         assert not bad.any() or np.abs(gap[bad]).max() < BAND, q
         mismatches += int(bad.sum())
@@ -92,6 +93,36 @@ def test_word_tile_lockstep(T, int_weights):
     assert _lockstep(pbit.ALG_SPSA, T=T, steps=6, int_weights=int_weights) <= 2
     assert _lockstep(pbit.ALG_TAPSA, T=T, steps=6, int_weights=int_weights) <= 2
     assert _lockstep(pbit.ALG_PSA, T=T, steps=12, t_res=10, nu_dev=nu, int_weights=int_weights) <= 2
+
+
+@pytest.mark.parametrize("mode", [pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
+def test_word_tile_offset_modes_and_bias(mode):
+    """The word tile (T = 256) in the other two offset placements, with biases h, against the oracle."""
+    nu = np.random.default_rng(4).normal(0, 0.5, 500).astype(np.float32)
+    assert _lockstep(pbit.ALG_SPSA, T=256, steps=5, mode=mode, bias=True) <= 2
+    assert _lockstep(pbit.ALG_TAPSA, T=256, steps=5, mode=mode, bias=True) <= 2
+    assert _lockstep(pbit.ALG_PSA, T=256, steps=10, t_res=10, nu_dev=nu, mode=mode, bias=True) <= 2
+    assert _lockstep(pbit.ALG_TAPSA, T=128, steps=10, t_res=10, nu_dev=nu, mode=mode, bias=True,
+                     int_weights=True) <= 2
+
+
+def test_word_tile_misaligned_state_falls_back():
+    """A state buffer that is not 16-byte aligned sends SpSA to the group tile; results are the same."""
+    g = inputs.torus_2d(20, 30, 6, "pm1")
+    G = pbit.Graph.from_inputs(g)
+    T, S = 128, 12
+    nbytes = pbit.pbit_variant_state_bytes(g.n, T, pbit.ALG_SPSA, 4)
+    outs, states = [], []
+    for off in (0, 4):
+        raw = torch.zeros(nbytes + 16, dtype=torch.uint8, device="cuda")
+        st = raw[off:off + nbytes]
+        out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+        p, keep = pbit.make_params(T, S, seed=3, algorithm=pbit.ALG_SPSA, state=st)
+        pbit.pbit_anneal(G.handle, p, None, out)
+        outs.append(_host(out))
+        states.append(_host(st))
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(states[0], states[1])
 
 
 @pytest.mark.parametrize("T,spread", [(128, 0.15), (1024, 0.15), (96, 0.15), (256, 3.0)])
