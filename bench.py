@@ -41,13 +41,13 @@ TRAFFIC = {
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
                            "sha": "5fedf916d58b284d", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
     # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
-    "sparse_variant_words_kernel:spsa": {"bytes": 103567189 + 41314645,
+    "sparse_variant_words_kernel:spsa": {"bytes": 103571712 + 41216256,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "d5731523a7973f95",
+                                         "sha": "e25655752a329a68",
                                          "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
-    "sparse_variant_words_kernel:tapsa": {"bytes": 144540245 + 35561813,
+    "sparse_variant_words_kernel:tapsa": {"bytes": 144522837 + 35485866,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "d5731523a7973f95",
+                                          "sha": "e25655752a329a68",
                                           "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
     # per launch of a 64-step chunk of all 64 instances
     "batch_chunk_kernel": {"bytes": 811351552 + 1346066432, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],

@@ -217,7 +217,11 @@ __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words
                 make_uint2((uint32_t)(uint16_t)d16[0] | ((uint32_t)(uint16_t)d16[1] << 16),
                            (uint32_t)(uint16_t)d16[2] | ((uint32_t)(uint16_t)d16[3] << 16));
 #pragma unroll
-            for (int b = 0; b < 4; ++b) I[b] = __fmul_rn(I0, __fdiv_rn((float)sum[b], (float)a.window));
+            for (int b = 0; b < 4; ++b) {
+                // sum / window: for the paper's window of 4 a multiply by 0.25, exact like the division
+                const float mean = WIN == 4 ? __fmul_rn((float)sum[b], 0.25f) : __fdiv_rn((float)sum[b], (float)a.window);
+                I[b] = __fmul_rn(I0, mean);
+            }
         } else {
 #pragma unroll
             for (int b = 0; b < 4; ++b) I[b] = __fmul_rn(I0, (float)D[4 * k + b]);
