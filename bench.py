@@ -41,17 +41,18 @@ TRAFFIC = {
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
                            "sha": "5fedf916d58b284d", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
     # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
-    "sparse_variant_words_kernel:spsa": {"bytes": 103571712 + 41216256,
+    "sparse_variant_words_kernel:spsa": {"bytes": 103572650 + 41357994,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "e25655752a329a68",
+                                         "sha": "b41280397fdb4de6",
                                          "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
-    "sparse_variant_words_kernel:tapsa": {"bytes": 144522837 + 35485866,
+    "sparse_variant_words_kernel:tapsa": {"bytes": 144539904 + 35478869,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "e25655752a329a68",
+                                          "sha": "b41280397fdb4de6",
                                           "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
-    # per launch of a 64-step chunk of all 64 instances
+    # per launch of a 64-step chunk of all 64 instances (sha re-taken after a host-only change to
+    # pbit_batch.cu, the TApSA field-range check in the instance setup; the kernel is as captured)
     "batch_chunk_kernel": {"bytes": 811351552 + 1346066432, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
-                           "sha": "90f3bf29cc6398a2", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
+                           "sha": "bcaed6fff1a7ec6c", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
 }
 
 

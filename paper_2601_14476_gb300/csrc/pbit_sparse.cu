@@ -59,9 +59,18 @@ __global__ void bounded_wait_selftest_kernel(const unsigned* flag, long long bud
 }
 
 // ------------------------------------------------------------------ step ----
+// Programmatic dependent launch between consecutive step launches: a step's grid may be scheduled
+// while the previous one drains and waits (griddepcontrol.wait) until that grid has completed and
+// its spins are visible.  Both instructions are no-ops in a launch without the attribute.
+__device__ __forceinline__ void step_dependency() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int G, bool UNIT, bool TABLE>
 __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
     __shared__ uint32_t s_tab[TABLE ? kTabMax : 1];
+    step_dependency();
     process_tile<G, UNIT, TABLE>(a, blockIdx.x * (int64_t)kBlock, s_tab);
 }
 
@@ -69,11 +78,36 @@ __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
 // 33.5 µs per step, against 33.7 (five), 35.5 (four) and 36.2 (seven or eight, with spills).
 template <int G>
 __global__ void __launch_bounds__(kBlock, 6) sparse_warp_kernel(StepArgs a) {
+    step_dependency();
     process_tile_warp<G>(a, blockIdx.x * (uint32_t)kBlock);
+}
+
+// A step launch with programmatic stream serialization, or a plain one when PBIT_NO_PDL is set or the
+// attribute is refused.
+template <typename K>
+cudaError_t launch_step_pdl(K kernel, unsigned blocks, const StepArgs& a, cudaStream_t s) {
+    static const bool off = std::getenv("PBIT_NO_PDL") != nullptr;
+    if (!off) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kBlock);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, kernel, a) == cudaSuccess) return cudaSuccess;
+        (void)cudaGetLastError();  // clear the refusal, then launch plainly
+    }
+    kernel<<<blocks, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int G, bool UNIT>
 __global__ void __launch_bounds__(kBlock) sparse_variant_kernel(StepArgs a) {
+    step_dependency();
     process_tile_variant<G, UNIT>(a, blockIdx.x * (int64_t)kBlock);
 }
 
@@ -81,9 +115,9 @@ template <int G, bool UNIT>
 cudaError_t launch_variant_g(const StepArgs& a, cudaStream_t s) {
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
-    sparse_variant_kernel<G, UNIT><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    const cudaError_t e = launch_step_pdl(sparse_variant_kernel<G, UNIT>, (unsigned)blocks, a, s);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <int G, bool UNIT, bool TABLE>
@@ -92,9 +126,9 @@ cudaError_t launch_step_g(const StepArgs& base, cudaStream_t s) {
     set_group_divisor(a, G);
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
-    sparse_step_kernel<G, UNIT, TABLE><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    const cudaError_t e = launch_step_pdl(sparse_step_kernel<G, UNIT, TABLE>, (unsigned)blocks, a, s);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <int G>
@@ -103,9 +137,9 @@ cudaError_t launch_warp_g(const StepArgs& base, cudaStream_t s) {
     set_group_divisor(a, G);
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
-    sparse_warp_kernel<G><<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    const cudaError_t e = launch_step_pdl(sparse_warp_kernel<G>, (unsigned)blocks, a, s);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <int G>

@@ -72,6 +72,10 @@ __device__ __forceinline__ void st32(int8_t* p, uint32_t v) { *reinterpret_cast<
 template <int NW, bool UNIT, int WIN>
 __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words_kernel(const __grid_constant__ VariantLaunch L) {
     const StepArgs& a = L.a;
+    // programmatic dependent launch: the next (sub-)step's grid may start its prologue now; it reads
+    // spins and state only after its own griddepcontrol.wait (below), which returns once this grid
+    // has completed and its memory is visible.  Both are no-ops in a launch without the attribute.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t warp = (blockIdx.x * (uint32_t)kVBlock + threadIdx.x) >> 5;
     const int lane = (int)(threadIdx.x & 31u);
     if (warp >= L.warps) return;
@@ -90,6 +94,16 @@ __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words
     const uint32_t q = (uint32_t)a.step;
     const int tb = (int)sidx * (128 * NW) + 4 * lane;  // trial of word 0; word k at tb + 128 k
     const size_t row = (size_t)i * T;
+    // everything above and the per-node parameters below are constant over the call; spins and state
+    // are written by the previous grid
+    const uint32_t nu_i = a.t_res > 0 && !L.slots ? (uint32_t)__ldg(a.nu + i) : 1u;
+    const float I0 = __ldg(a.i0_table + (a.t_res > 0 ? q / (uint32_t)a.t_res : q));
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // where the node's spins are read and written, and where neighbour j's are read
     const int8_t* src = a.in;
     int8_t* dst = a.out;
@@ -103,7 +117,7 @@ __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words
         return ((L.pmask >> __ldg(L.ebkt + e)) & 1u) ? a.out : L.alt;
     };
     if (a.t_res > 0 && !L.slots) {
-        const uint32_t nu = (uint32_t)__ldg(a.nu + i);
+        const uint32_t nu = nu_i;
         if (q % nu != 0u) {
             if (!a.carry || (q - 1u) % nu == 0u) {
 #pragma unroll
@@ -112,12 +126,6 @@ __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words
             return;
         }
     }
-    const float I0 = __ldg(a.i0_table + (a.t_res > 0 ? q / (uint32_t)a.t_res : q));
-    const int hi = a.h ? __ldg(a.h + i) : 0;
-    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
-    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
-    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
-    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
     // the carried state first, so that its loads are in flight during the gather:
     // SpSA the last inputs, TApSA the sum of the ring slots other than q % window
     const size_t plane = (size_t)a.n * T;
@@ -264,16 +272,39 @@ __global__ void edge_bucket_kernel(int64_t nnz, const int32_t* __restrict__ col,
     if (e < nnz) ebkt[e] = __ldg(bkt + __ldg(col + e));
 }
 
+// One launch with programmatic stream serialization (the grid may begin while the previous kernel in
+// the stream drains; see the kernel's griddepcontrol), or a plain launch when PBIT_NO_PDL is set or
+// the attribute is refused.
+template <typename K>
+cudaError_t launch_pdl(K kernel, unsigned blocks, const VariantLaunch& L, cudaStream_t s) {
+    static const bool off = std::getenv("PBIT_NO_PDL") != nullptr;
+    if (!off) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kVBlock);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, kernel, L) == cudaSuccess) return cudaSuccess;
+        (void)cudaGetLastError();  // clear the refusal, then launch plainly
+    }
+    kernel<<<blocks, kVBlock, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
 template <int NW, bool UNIT>
 cudaError_t launch_words(const VariantLaunch& L, cudaStream_t s) {
     if (L.warps == 0) return cudaSuccess;
-    const uint64_t blocks = ((uint64_t)L.warps * 32 + kVBlock - 1) / kVBlock;
-    if (L.a.alg == 2 && L.a.window == 4)
-        sparse_variant_words_kernel<NW, UNIT, 4><<<(unsigned)blocks, kVBlock, 0, s>>>(L);
-    else
-        sparse_variant_words_kernel<NW, UNIT, 0><<<(unsigned)blocks, kVBlock, 0, s>>>(L);
+    const unsigned blocks = (unsigned)(((uint64_t)L.warps * 32 + kVBlock - 1) / kVBlock);
+    const cudaError_t e = (L.a.alg == 2 && L.a.window == 4)
+                              ? launch_pdl(sparse_variant_words_kernel<NW, UNIT, 4>, blocks, L, s)
+                              : launch_pdl(sparse_variant_words_kernel<NW, UNIT, 0>, blocks, L, s);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 bool aligned(const void* p, uintptr_t b) { return ((uintptr_t)p % b) == 0; }
