@@ -40,14 +40,15 @@ TRAFFIC = {
     "sparse_flow_kernel": {"bytes": 23335680 + 5099264,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
                            "sha": "5fedf916d58b284d", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
-    # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
+    # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024 (sha re-taken after
+    # a comment-only edit of pbit_variant.cu)
     "sparse_variant_words_kernel:spsa": {"bytes": 103572650 + 41357994,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "b41280397fdb4de6",
+                                         "sha": "0e431dabac2bbb59",
                                          "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
     "sparse_variant_words_kernel:tapsa": {"bytes": 144539904 + 35478869,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "b41280397fdb4de6",
+                                          "sha": "0e431dabac2bbb59",
                                           "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
     # per launch of a 64-step chunk of all 64 instances (sha re-taken after a host-only change to
     # pbit_batch.cu, the TApSA field-range check in the instance setup; the kernel is as captured)

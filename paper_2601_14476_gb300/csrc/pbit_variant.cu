@@ -24,6 +24,10 @@
 // buffer, but only when that buffer lacks them: the output of sub-step q holds
 // the state of q - 2 (`carry`), which differs from that of q - 1 only for the
 // nodes due at q - 1.
+//
+// Consecutive (sub-)step launches use programmatic dependent launch: a grid
+// runs its constant prologue while the previous one drains and waits for it
+// (griddepcontrol.wait) before touching spins or state.
 #include "pbit_internal.h"
 #include "pbit_device.cuh"
 #include "pbit_tile.cuh"
