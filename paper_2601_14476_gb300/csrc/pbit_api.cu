@@ -621,7 +621,7 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
     if (kernel == PBIT_KERNEL_RESIDENT) {
         a.in = cur;
         a.out = spins_out;
-        PBIT_CUDA_TRY(launch_resident_anneal(a, b, e, s));
+        PBIT_CUDA_TRY(launch_resident_anneal(a, b, e, g->unit_weights && g->max_degree <= 127, s));
         return PBIT_OK;
     }
     if (kernel == PBIT_KERNEL_DENSE) {

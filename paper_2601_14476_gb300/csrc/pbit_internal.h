@@ -199,7 +199,7 @@ bool resident_fits(const Graph& g, int32_t T);
 // on GB300: G(800, 19176), T = 16 runs 5.8 µs per step resident on the cluster, 32 µs on one CTA,
 // 12.4 µs sparse), so the break-even is about 1.3e6 gathers per step.
 bool resident_preferred(const Graph& g, int32_t T);
-cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end,
+cudaError_t launch_resident_anneal(const StepArgs& base, int32_t step_begin, int32_t step_end, bool unit,
                                    cudaStream_t s);
 
 }  // namespace pbit

@@ -165,7 +165,9 @@ constexpr int kResidentThreads = 512;
 constexpr size_t kResidentSmem = 200 * 1024;
 constexpr int kResidentCluster = 8;
 
-template <int G>
+// UNIT (weights +-1, degree <= 127, G = 4): the field is counted four trials at a time as in the
+// tiles (2 per neighbour with J_ij s_j = -1, one 32-bit shared-memory load per neighbour).
+template <int G, bool UNIT>
 __global__ void __launch_bounds__(kResidentThreads) resident_kernel(StepArgs a, int32_t step_begin, int32_t step_end) {
     extern __shared__ __align__(16) int8_t smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -177,17 +179,30 @@ __global__ void __launch_bounds__(kResidentThreads) resident_kernel(StepArgs a, 
     cluster.sync();  // every CTA runs (and holds the state) before any peer writes into it
     const int groups = a.T / G;
     const int node_lo = (int)((int64_t)a.n * r / C), node_hi = (int)((int64_t)a.n * (r + 1) / C);
-    const int64_t items = (int64_t)(node_hi - node_lo) * groups;
+    const int items = (node_hi - node_lo) * groups;  // < 2^31: both spin copies fit in shared memory
     int8_t* cur = buf0;
     int8_t* nxt = buf1;
     for (int32_t step = step_begin; step < step_end; ++step) {
         StepArgs sa = a;
         sa.step = step;
-        for (int64_t it = threadIdx.x; it < items; it += blockDim.x) {
-            const int i = node_lo + (int)(it / groups);
-            const int t0 = (int)(it - (int64_t)(i - node_lo) * groups) * G;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int li = it / groups;
+            const int i = node_lo + li;
+            const int t0 = (it - li * groups) * G;
             int acc[G];
-            gather_field<G>(a.row_ptr, a.col, a.J, cur, a.T, i, t0, acc);
+            if constexpr (UNIT && G == 4) {
+                const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+                uint32_t cnt2 = 0;
+                for (int e = rb; e < re; ++e) {
+                    const int8_t* pj = cur + (size_t)__ldg(a.col + e) * a.T + t0;
+                    const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
+                    cnt2 += (*reinterpret_cast<const uint32_t*>(pj) & 0x02020202u) ^ flip;
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k) acc[k] = (re - rb) - (int)((cnt2 >> (8 * k)) & 0xFFu);
+            } else {
+                gather_field<G>(a.row_ptr, a.col, a.J, cur, a.T, i, t0, acc);
+            }
             uint32_t oldw[Pack<G>::W], neww[Pack<G>::W];
             const size_t off = (size_t)i * a.T + t0;
             load_group<G>(cur + off, oldw);
@@ -203,11 +218,11 @@ __global__ void __launch_bounds__(kResidentThreads) resident_kernel(StepArgs a, 
     for (int64_t c = (int64_t)node_lo * a.T + threadIdx.x; c < (int64_t)node_hi * a.T; c += blockDim.x) a.out[c] = cur[c];
 }
 
-template <int G>
+template <int G, bool UNIT>
 cudaError_t launch_resident_g(const StepArgs& a, int32_t b, int32_t e, cudaStream_t s) {
     const int64_t cells = (int64_t)a.n * a.T;
     const size_t smem = 2 * (size_t)(((cells + 15) / 16) * 16);
-    cudaError_t err = cudaFuncSetAttribute(resident_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(resident_kernel<G, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)kResidentSmem);
     if (err != cudaSuccess) return err;
     static const char* cl_env = std::getenv("PBIT_RESIDENT_CLUSTER");  // tests: 1 forces one CTA
@@ -225,15 +240,15 @@ cudaError_t launch_resident_g(const StepArgs& a, int32_t b, int32_t e, cudaStrea
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (want > 1 && cudaOccupancyMaxActiveClusters(&clusters, resident_kernel<G>, &cfg) == cudaSuccess && clusters >= 1) {
-        err = cudaLaunchKernelEx(&cfg, resident_kernel<G>, a, b, e);
+    if (want > 1 && cudaOccupancyMaxActiveClusters(&clusters, resident_kernel<G, UNIT>, &cfg) == cudaSuccess && clusters >= 1) {
+        err = cudaLaunchKernelEx(&cfg, resident_kernel<G, UNIT>, a, b, e);
         count_launches(1);
         return err;
     }
     (void)cudaGetLastError();
     cfg.gridDim = dim3(1, 1, 1);
     attr[0].val.clusterDim.x = 1;
-    err = cudaLaunchKernelEx(&cfg, resident_kernel<G>, a, b, e);
+    err = cudaLaunchKernelEx(&cfg, resident_kernel<G, UNIT>, a, b, e);
     count_launches(1);
     return err;
 }
@@ -426,9 +441,9 @@ bool resident_fits(const Graph& g, int32_t T) {
     return 2 * (((cells + 15) / 16) * 16) <= (int64_t)kResidentSmem;
 }
 
-cudaError_t launch_resident_anneal(const StepArgs& a, int32_t b, int32_t e, cudaStream_t s) {
-    if (a.T % 4 == 0) return launch_resident_g<4>(a, b, e, s);
-    return launch_resident_g<1>(a, b, e, s);
+cudaError_t launch_resident_anneal(const StepArgs& a, int32_t b, int32_t e, bool unit, cudaStream_t s) {
+    if (a.T % 4 == 0) return unit ? launch_resident_g<4, true>(a, b, e, s) : launch_resident_g<4, false>(a, b, e, s);
+    return launch_resident_g<1, false>(a, b, e, s);
 }
 
 cudaError_t launch_fields(const Graph& g, const int8_t* spins, int32_t T, int32_t* fields, cudaStream_t s) {
