@@ -52,6 +52,24 @@ def test_philox_matches_triton_interpreter():
         assert got == want, (ctr, key, got, want)
 
 
+def test_philox_output_statistics():
+    """2^16 blocks at consecutive trial counters: every bit set half the time, the top byte of each
+    word uniform (chi-square, 255 dof) and the top nibbles of the r and u words of one trial independent
+    (chi-square, 255 dof), both within five standard deviations."""
+    words = np.array([oracle.philox4x32_10([node, 3, t, 0], [0x1234, 0x9876])
+                      for node in range(16) for t in range(4096)], dtype=np.uint32)
+    flat = words.ravel()
+    bits = ((flat[:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 5 * np.sqrt(0.25 / flat.size))
+    sd = np.sqrt(2 * 255)
+    counts = np.bincount(flat >> 24, minlength=256)
+    e = flat.size / 256
+    assert abs(((counts - e) ** 2 / e).sum() - 255) < 5 * sd
+    pair = np.bincount(((words[:, 0] >> 28) << 4) | (words[:, 1] >> 28), minlength=256)
+    e = len(words) / 256
+    assert abs(((pair - e) ** 2 / e).sum() - 255) < 5 * sd
+
+
 def test_draw_grids():
     """r lies on the odd 2^24 midpoint grid of (-1,1); u on the 2^24 grid of [0,1)."""
     rs, us = [], []
