@@ -583,7 +583,7 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         int32_t* dp = nullptr;
         if ((st = cb.put(&dp, buckets.host_perm.data(), buckets.host_perm.size())) != PBIT_OK) return st;
         buckets.perm = dp;
-        if (!buckets.host_bkt.empty()) {
+        if (!buckets.host_bkt.empty() && T % 128 == 0) {  // the parity form needs the word tile
             uint8_t* db = nullptr;
             if ((st = cb.put(&db, buckets.host_bkt.data(), buckets.host_bkt.size())) != PBIT_OK) return st;
             buckets.bkt = db;
