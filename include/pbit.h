@@ -198,8 +198,11 @@ void pbit_anneal_params_default(pbit_anneal_params* p);
  * Stream-ordered on p->stream (this call does not wait for the GPU); it
  * allocates its scratch with cudaMallocAsync on that stream and copies the
  * per-node parameters from host memory, so it is not for use under stream
- * capture.  Errors: PBIT_E_INVALID, PBIT_E_UNSUPPORTED (forced kernel cannot
- * run the shape), PBIT_E_NOMEM, PBIT_E_CUDA.
+ * capture.  Scratch: at most two further n*T spin buffers, the variant state
+ * when p->state is NULL, and under the timing model 8n + 2m bytes of periods,
+ * node order and period buckets.  Errors: PBIT_E_INVALID, PBIT_E_UNSUPPORTED
+ * (forced kernel cannot run the shape; TApSA fields beyond int16),
+ * PBIT_E_NOMEM, PBIT_E_CUDA.
  */
 pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in, int8_t* spins_out);
 
