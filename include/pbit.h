@@ -198,7 +198,7 @@ void pbit_anneal_params_default(pbit_anneal_params* p);
  * Stream-ordered on p->stream (this call does not wait for the GPU); it
  * allocates its scratch with cudaMallocAsync on that stream and copies the
  * per-node parameters from host memory, so it is not for use under stream
- * capture.  Scratch: at most two further n*T spin buffers, the variant state
+ * capture.  Scratch: up to three n*T spin buffers, the variant state
  * when p->state is NULL, and under the timing model 8n + 2m bytes of periods,
  * node order and period buckets.  Errors: PBIT_E_INVALID, PBIT_E_UNSUPPORTED
  * (forced kernel cannot run the shape; TApSA fields beyond int16),
