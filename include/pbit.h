@@ -134,16 +134,18 @@ pbit_status pbit_mean_s(int32_t n, int64_t n_edges, const int32_t* src, const in
 /* ------------------------------------------------------------------------ */
 
 typedef enum {
-    PBIT_OFFSET_SCALED = 0, /* x = I0 * (lambda*D + delta) */
+    PBIT_OFFSET_SCALED = 0,    /* x = I0 * (lambda*D + delta) */
     PBIT_OFFSET_LISTING = 1,   /* x = lambda * I0 * (D + delta)   (the paper's pseudo code) */
     PBIT_OFFSET_EQUATION = 2   /* x = lambda * (I0*D + delta)     (Eq. 6 with Eq. 3) */
 } pbit_offset_mode;
 
 typedef enum {
     PBIT_KERNEL_AUTO = 0,      /* pick from the graph shape */
-    PBIT_KERNEL_SPARSE = 1,    /* CSR gather kernel, one launch per step */
+    PBIT_KERNEL_SPARSE = 1,    /* CSR gather kernel: one persistent launch with per-tile step
+                                  dependencies when they are local, else one launch per step */
     PBIT_KERNEL_DENSE = 2,     /* tensor-core field kernel (needs PBIT_GRAPH_DENSE) */
-    PBIT_KERNEL_RESIDENT = 3   /* whole anneal in one CTA with spins in shared memory */
+    PBIT_KERNEL_RESIDENT = 3   /* whole anneal in one launch on a cluster of up to 8 CTAs, each
+                                  holding all spins in shared memory (2*n*T <= 200 KB) */
 } pbit_kernel;
 
 typedef struct {
