@@ -34,8 +34,8 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes per launch of each dominant kernel from one ncu capture (profiles/*.md), valid only while
 # the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
 TRAFFIC = {
-    "dense_persistent_kernel": {"bytes": 5234944 + 184064, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "36f00a53d801a421",
+    "dense_persistent_kernel": {"bytes": 5231616 + 241408, "files": ["pbit_dense.cu", "pbit_device.cuh"],
+                                "sha": "e370568a61cc0ba7",
                                 "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
     "sparse_flow_kernel": {"bytes": 23335680 + 5099264,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],

@@ -583,14 +583,29 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                     const int r0 = (it & 31) * 4;
                     const int lc0 = 2 * (pb + (it >> 5));
                     int f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
-                    for (int src = 0; src < a.KS; ++src) {
-                        const int16_t* rp = cluster.map_shared_rank(part, src);
-                        const uint2 x = *reinterpret_cast<const uint2*>(rp + (size_t)lc0 * kRows + r0);
-                        const uint2 y = *reinterpret_cast<const uint2*>(rp + (size_t)(lc0 + 1) * kRows + r0);
+                    const auto add = [&](const uint2 x, const uint2 y) {
                         f0[0] += (int16_t)(x.x & 0xFFFF); f0[1] += (int16_t)(x.x >> 16);
                         f0[2] += (int16_t)(x.y & 0xFFFF); f0[3] += (int16_t)(x.y >> 16);
                         f1[0] += (int16_t)(y.x & 0xFFFF); f1[1] += (int16_t)(y.x >> 16);
                         f1[2] += (int16_t)(y.y & 0xFFFF); f1[3] += (int16_t)(y.y >> 16);
+                    };
+                    const size_t o0 = (size_t)lc0 * kRows + r0, o1 = o0 + kRows;
+                    if (a.KS == 4) {
+                        // all eight remote loads issued before the first sum: one DSMEM round trip
+                        uint2 x[4], y[4];
+#pragma unroll
+                        for (int src = 0; src < 4; ++src) {
+                            const int16_t* rp = cluster.map_shared_rank(part, src);
+                            x[src] = *reinterpret_cast<const uint2*>(rp + o0);
+                            y[src] = *reinterpret_cast<const uint2*>(rp + o1);
+                        }
+#pragma unroll
+                        for (int src = 0; src < 4; ++src) add(x[src], y[src]);
+                    } else {
+                        for (int src = 0; src < a.KS; ++src) {
+                            const int16_t* rp = cluster.map_shared_rank(part, src);
+                            add(*reinterpret_cast<const uint2*>(rp + o0), *reinterpret_cast<const uint2*>(rp + o1));
+                        }
                     }
                     const int t0 = tb * NT + lc0;
                     const int i0 = rb * kRows + r0;
