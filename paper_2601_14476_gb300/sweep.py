@@ -97,10 +97,13 @@ def main(argv=None):
     ap.add_argument("--trials", type=int, default=64)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--algorithm", default="psa", choices=["psa", "spsa", "tapsa"],
+                    help="pSA, SpSA (stall probability 0.5) or TApSA (window 4) at every grid point")
     args = ap.parse_args(argv)
     g = (inputs.erdos_renyi_gnm(800, 19176, args.seed, "+1") if args.graph == "gnm800"
          else inputs.torus_2d(100, 200, args.seed, "pm1"))
-    for rec in variability_sweep(g, default_grid(), args.trials, args.steps, seed=args.seed):
+    extra = {"algorithm": {"psa": pbit.ALG_PSA, "spsa": pbit.ALG_SPSA, "tapsa": pbit.ALG_TAPSA}[args.algorithm]}
+    for rec in variability_sweep(g, default_grid(), args.trials, args.steps, seed=args.seed, **extra):
         print({**asdict(rec["point"]), "mean_cut": round(rec["mean_cut"], 2), "best_cut": rec["best_cut"]})
 
 
