@@ -262,3 +262,21 @@ def test_variant_full_run_matches_oracle(alg, t_res):
     ref_cut = oracle.cut(g.src, g.dst, g.w, ref)
     assert (gpu_cut == ref_cut).mean() >= 0.75, (gpu_cut, ref_cut)
     assert abs(gpu_cut.mean() - ref_cut.mean()) <= 0.005 * abs(ref_cut.mean())
+
+
+@pytest.mark.parametrize("alg", [pbit.ALG_PSA, pbit.ALG_SPSA, pbit.ALG_TAPSA])
+def test_variants_on_degenerate_graphs(alg):
+    """No edges (fields = biases only, empty edge-bucket array) and a single node, T = 128 (word tile;
+    parity form under the timing model): one call equals the oracle step by step from the same start."""
+    cases = [(pbit.Graph(9, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8),
+                         h=np.arange(9, dtype=np.int32) - 4), 9, np.arange(9, dtype=np.int32) - 4),
+             (pbit.Graph(1, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8)), 1, None)]
+    for G, n, h in cases:
+        T, S, t_res = 128, 6, 10
+        nu = np.linspace(-0.3, 0.3, n).astype(np.float32)
+        kw = dict(algorithm=alg, t_res=t_res, nu_dev=nu, window=4)
+        out = _host(G.anneal(T, S, seed=3, i0_normalize=0, i0_min=0.1, i0_max=2.0, **kw))
+        csr = oracle.Csr(n, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int8))
+        tab = oracle.i0_table(0.1, 2.0, S)
+        ref, _ = oracle.anneal_variant(csr, oracle.init_spins(n, T, 3), tab, 3, h=h, **kw)
+        assert (out == ref).mean() >= 0.99, (n, (out != ref).sum())
