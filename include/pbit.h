@@ -211,21 +211,25 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
 /*
  * pbit_anneal without any device allocation (the paper has no counterpart;
  * this is a deployment variant of pbit_anneal).  For callers that cannot
- * allocate device memory while they run: code inside stream callbacks or
- * host functions (where CUDA API allocation calls are not allowed),
- * applications whose own allocator has reserved nearly all of HBM, and
- * latency-bound loops that cannot absorb an allocation's synchronisation.
- * Same arguments, results and Philox stream as pbit_anneal with
- * kernel = PBIT_KERNEL_SPARSE (p->kernel is ignored).  All scratch lives in
- * one fixed 32 MiB device array inside libpbit.so, held on every GPU that
- * loads the library until the process exits; the call needs
- * 4*steps + 12*n + n*trials bytes of it (each part rounded up to 256) and
- * returns PBIT_E_INVALID, with the sizes in pbit_last_error(), when that is
- * more.  It calls no cudaMalloc/cudaFree.  The first call on each device
- * looks up the array's device address once (cudaGetSymbolAddress); make that
- * first call before any stream capture begins.  Every call reuses the same
- * array, so calls whose GPU work overlaps (e.g. on two streams) race and
- * must be serialised by the caller.
+ * allocate device memory while they run: applications whose own caching
+ * allocator has reserved nearly all of HBM up front (a library cudaMalloc
+ * would fail or take memory promised elsewhere), processes under a fixed
+ * device-memory cap, and latency-bound loops that cannot absorb an
+ * allocation's synchronisation.  Same arguments, results and Philox stream
+ * as pbit_anneal with kernel = PBIT_KERNEL_SPARSE (p->kernel is ignored;
+ * plain pSA only, else PBIT_E_UNSUPPORTED); every step runs the graph's
+ * per-step sparse tile.  All scratch lives in one fixed 32 MiB device array
+ * inside libpbit.so, held on every GPU that loads the library until the
+ * process exits; the call needs 4*steps + 12*n + n*trials bytes of it (each
+ * part rounded up to 256) and returns PBIT_E_INVALID, with the sizes in
+ * pbit_last_error(), when that is more.  It calls no cudaMalloc/cudaFree.
+ * It does call the CUDA runtime (the array's address is looked up with
+ * cudaGetSymbolAddress on every call; parameters are uploaded with
+ * cudaMemcpyAsync from pageable host memory), so it must not be called from
+ * a stream callback or host function, and, like pbit_anneal, it is not for
+ * use under stream capture.  Non-finite intensity or offset values give
+ * PBIT_E_INVALID.  Every call reuses the same array, so calls whose GPU work
+ * overlaps (e.g. on two streams) race and must be serialised by the caller.
  */
 pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_params* p, const int8_t* spins_in,
                                 int8_t* spins_out);

@@ -2,12 +2,20 @@
 // a fixed, file-scope device array instead of memory allocated per call.
 //
 // Who needs this: callers that must not allocate device memory while they
-// run.  Examples are code that executes inside a stream callback or host
-// function (the CUDA runtime forbids API calls such as cudaMalloc there),
-// applications whose own caching allocator has reserved nearly all of HBM up
-// front (a cudaMalloc from a library would fail or fragment their pool), and
-// latency-bound service loops that cannot afford the implicit
-// synchronisation and unbounded latency an allocation may bring.
+// run.  Examples are applications whose own caching allocator has reserved
+// nearly all of HBM up front (a cudaMalloc from a library would fail, or
+// would take memory the application has already promised elsewhere),
+// processes that run under a fixed device-memory cap, and latency-bound
+// service loops that cannot afford the implicit synchronisation and
+// unbounded latency an allocation may bring.
+//
+// What it still does: it calls the CUDA runtime (cudaGetDevice,
+// cudaGetSymbolAddress, cudaMemcpyAsync, kernel launches), so it must not be
+// called from a stream callback or host function, where CUDA forbids every
+// API call; and its parameter uploads (I0 table, intensity, offset, update
+// thresholds) are cudaMemcpyAsync copies from pageable host memory, which
+// the runtime stages synchronously, so the call is not meant for stream
+// capture (the same as pbit_anneal).
 //
 // The scratch array is kNoAllocScratchBytes (32 MiB) of global memory,
 // reserved on every GPU that loads libpbit.so until the process exits.
@@ -17,11 +25,15 @@
 // nothing in it has to start at zero and nothing is cleared.  Every call
 // reuses the same array and leaves the last call's data in it; two calls
 // whose GPU work overlaps (for example on two streams) race on it.
+//
+// The steps run the graph's per-step sparse tile (packed +-1 counting, the
+// threshold table or the warp-table tile, as pbit_anneal picks them); the
+// multi-step launch is not used, because its dependency lists and counters
+// are allocated memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,24 +46,16 @@ constexpr size_t kNoAllocScratchBytes = 32u << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
 // Device address of the scratch array on the current device.  Host code sees
 // only a host-side stand-in under the array's name, so the real address is
-// looked up once per device with cudaGetSymbolAddress while that device is
-// current, and cached.
-pbit_status scratch_address(int device, unsigned char** out) {
-    if (device < 0 || device >= kMaxDevices) return fail(PBIT_E_INVALID, "anneal_noalloc: device ordinal too large");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "anneal_noalloc: cudaGetSymbolAddress");
-        g_noalloc_ptr[device] = p;
-    }
-    *out = static_cast<unsigned char*>(g_noalloc_ptr[device]);
+// looked up with cudaGetSymbolAddress while the graph's device is current.
+// The lookup allocates nothing and is repeated on every call, so no cached
+// address can outlive a cudaDeviceReset.
+pbit_status scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "anneal_noalloc: cudaGetSymbolAddress");
+    *out = static_cast<unsigned char*>(p);
     return PBIT_OK;
 }
 
@@ -103,9 +107,15 @@ extern "C" pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_param
             thr[i] = (uint32_t)std::ceil((double)pu * 16777216.0);
         }
     }
+    if (p->intensity)
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(p->intensity[i])) return fail(PBIT_E_INVALID, "anneal_noalloc: non-finite intensity");
+    if (p->offset)
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(p->offset[i])) return fail(PBIT_E_INVALID, "anneal_noalloc: non-finite offset");
 
     unsigned char* base = nullptr;
-    if ((st = scratch_address(device, &base)) != PBIT_OK) return st;
+    if ((st = scratch_address(&base)) != PBIT_OK) return st;
     cudaStream_t s = (cudaStream_t)p->stream;
 
     StepArgs a{};
@@ -113,6 +123,8 @@ extern "C" pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_param
     a.col = gr->col;
     a.J = gr->J;
     a.h = gr->h;
+    a.wabs = gr->wabs;
+    a.tab_off = gr->tab_off;
     a.n = gr->n;
     a.T = T;
     a.seed_lo = (uint32_t)(p->seed & 0xFFFFFFFFu);
@@ -156,12 +168,13 @@ extern "C" pbit_status pbit_anneal_noalloc(pbit_graph g, const pbit_anneal_param
         PBIT_CUDA_TRY(cudaMemcpyAsync(scratch, cur, cells, cudaMemcpyDeviceToDevice, s));
         cur = scratch;
     }
+    const SparseVariant v = choose_sparse_variant(*gr, T);
     for (int32_t j = 0; j < k; ++j) {
         int8_t* dst = ((k - 1 - j) % 2 == 0) ? spins_out : scratch;
         a.step = b + j;
         a.in = cur;
         a.out = dst;
-        PBIT_CUDA_TRY(launch_sparse_step(a, s));
+        PBIT_CUDA_TRY(launch_sparse_step(a, s, v));
         cur = dst;
     }
     return PBIT_OK;

@@ -54,3 +54,30 @@ def test_noalloc_rejects_sizes_beyond_its_array():
         pbit.pbit_anneal_noalloc(G.handle, p, None, out)
     assert ei.value.code == pbit.PBIT_E_INVALID
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_fresh_start_with_odd_step_count():
+    """spins_in NULL with an odd number of steps: the initial state goes to the scratch buffer first
+    and the Jacobi rotation must still end in spins_out."""
+    g = inputs.rgg_knn(700, 3, 3, "pm1")
+    var = inputs.variability(g.n, 3)
+    G = pbit.Graph.from_inputs(g)
+    for T, lo, hi in ((32, 0, 13), (48, 4, 21), (16, 0, 1)):
+        kw = dict(seed=5, variability=var, step_begin=lo, step_end=hi, kernel=pbit.KERNEL_SPARSE)
+        want = _run(pbit.pbit_anneal, G, T, 30, None, **kw)
+        got = _run(pbit.pbit_anneal_noalloc, G, T, 30, None, **kw)
+        assert np.array_equal(got, want), (T, lo, hi)
+
+
+def test_noalloc_rejects_non_finite_parameters():
+    g = inputs.torus_2d(10, 10, 1, "pm1")
+    G = pbit.Graph.from_inputs(g)
+    out = torch.empty((g.n, 16), dtype=torch.int8, device="cuda")
+    for key in ("intensity", "offset"):
+        var = inputs.variability(g.n, 1)
+        var[key] = var[key].copy()
+        var[key][5] = np.nan if key == "intensity" else np.inf
+        p, keep = pbit.make_params(16, 10, seed=1, variability=var)
+        with pytest.raises(pbit.PbitError) as ei:
+            pbit.pbit_anneal_noalloc(G.handle, p, None, out)
+        assert ei.value.code == pbit.PBIT_E_INVALID
