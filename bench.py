@@ -1,14 +1,18 @@
 """Benchmark: spin-updates/s of the p-bit annealing hot path on GB300.
 
-One "step" of this benchmark is one complete anneal of the workload (every
-schedule step of every trial) followed by the exact per-trial cut, on inputs
-already resident in HBM.  The default workload is the dense one: K_2000 with
-w in {-1,+1}, 256 trials, 2000 steps, I0 0.05->5, variability on
-(intensity ~ N(1, 0.1^2), offset ~ N(0, 0.1^2), update probability
-~ clip(N(0.9, 0.05^2), 0, 1)).  Other workloads: --config sparse (100x200
-torus, 1024 trials, 5000 steps), plain (G(800,19176), 16 trials, 1000 steps,
-ideal p-bits).
+Default (``--config headline``): the uneven batch of 64 MAX-CUT instances
+(n log-uniform in [800, 10000], half G(n, 3n) with w = +1, half 3-NN random
+geometric graphs with w in {-1,+1}; 32/64/128/256 trials; 2000 steps;
+variability on), one "step" being one complete batched anneal of all 64
+instances followed by their exact cuts, on inputs already resident in HBM.
+The same line carries the plain one-instance-per-launch form of the same
+work on the same GPU (identical cuts), the oracle's whole-anneal mean cut of
+the two smallest instances on the same seeds (the "equal mean cut" check),
+the Poisson serving sweep (p50/p99 latency per arrival rate, saturation
+rate) and two single-instance components with their own rooflines: the dense
+K_2000 anneal on the tensor cores and the sparse 100x200 torus anneal.
 
+Other workloads: --config dense | sparse | plain | batch | serve | sweep.
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle as
 the reference arm on a bounded sample of the same workload.
 """
@@ -31,29 +35,26 @@ from paper_2601_14476_gb300 import inputs  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM bytes per launch of each dominant kernel from one ncu capture (profiles/*.md), valid only while
+# DRAM bytes (read + write) per launch of each dominant kernel from one ncu capture, valid only while
 # the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
 TRAFFIC = {
+    # one persistent launch: K_2000 +-1, 256 trials, 2000 steps
     "dense_persistent_kernel": {"bytes": 5231616 + 241408, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "e370568a61cc0ba7",
-                                "capture": "profiles/dense_persistent_kernel_complete2000_T256.md"},
+                                "sha": "e370568a61cc0ba7"},
+    # one multi-step launch: 100x200 torus, 1024 trials, 5000 steps
     "sparse_flow_kernel": {"bytes": 23335680 + 5099264,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
-                           "sha": "5fedf916d58b284d", "capture": "profiles/sparse_flow_kernel_torus100x200_T1024.md"},
-    # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024 (sha re-taken after
-    # a comment-only edit of pbit_variant.cu)
+                           "sha": "5fedf916d58b284d"},
+    # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
     "sparse_variant_words_kernel:spsa": {"bytes": 103572650 + 41357994,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "0e431dabac2bbb59",
-                                         "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
+                                         "sha": "0e431dabac2bbb59"},
     "sparse_variant_words_kernel:tapsa": {"bytes": 144539904 + 35478869,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "0e431dabac2bbb59",
-                                          "capture": "profiles/sparse_variant_words_kernel_torus100x200_T1024.md"},
-    # per launch of a 64-step chunk of all 64 instances (sha re-taken after a host-only change to
-    # pbit_batch.cu, the TApSA field-range check in the instance setup; the kernel is as captured)
+                                          "sha": "0e431dabac2bbb59"},
+    # per launch of a 64-step chunk of all 64 instances of the uneven batch
     "batch_chunk_kernel": {"bytes": 811351552 + 1346066432, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
-                           "sha": "bcaed6fff1a7ec6c", "capture": "profiles/batch_chunk_kernel_batch64.md", "chunk_steps": 64},
+                           "sha": "bcaed6fff1a7ec6c", "chunk_steps": 64},
 }
 
 
@@ -249,7 +250,7 @@ def _oracle_sample(job):
     import oracle
     kind, k = job
     if _ORACLE_CASE.get("kind") != kind:
-        w = multi_reference_workload(kind) if kind in ("batch", "sweep") else workload(kind)
+        w = multi_reference_workload(kind) if kind in ("batch", "sweep", "headline") else workload(kind)
         g = w.graph
         csr = oracle.Csr(g.n, g.src, g.dst, g.w)
         _ORACLE_CASE.update(kind=kind, w=w, csr=csr, tab=oracle.schedule(csr, w.c_min, w.c_max, w.steps),
@@ -307,7 +308,8 @@ def cpu_baseline(w, budget_s: float = 12.0, kind: str | None = None, all_cores: 
     return out
 
 
-def run_reference(args, w, variant=None):
+def run_reference(args, w, variant=None, config=None):
+    """The reference arm: the oracle as it stands, each step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -323,13 +325,13 @@ def run_reference(args, w, variant=None):
     line = {"impl": "reference", "metric": "spin-updates/s", "value": val, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * upd_run / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": workload_config(w),
+            "dtype": "f64", "data": "synthetic", "config": config or workload_config(w),
             "cpu_baseline": {**base, "value": val},
             "e2e": {"value": val, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------- batch and serve ----
+# ------------------------------------------------------------- plumbing ----
 
 def _dist_setup():
     import torch
@@ -374,124 +376,290 @@ def sweep_workloads(seed: int = 1, steps: int = 1000):
 
 def multi_reference_workload(config: str):
     """The single instance the oracle times for the multi-instance configs: the first batch instance
-    (batch, serve: requests come from the same generators) or the sweep point with all three spreads."""
-    return sweep_workloads()[-1] if config == "sweep" else inputs.batch64()[0]
+    (batch, headline, serve: requests come from the same generators) or the sweep point with all three
+    spreads."""
+    return sweep_workloads()[-1] if config == "sweep" else inputs.batch64(count=1)[0]
 
 
-def bench_multi(args):
-    """config batch: 64 uneven instances, batched persistent form vs plain one-instance-per-launch form.
-    config serve: Poisson request stream through the continuous-batching server, p50/p99 latency."""
+def batch_config(ws, wname):
+    """The keys that name the batched workload, shared by both bench arms."""
+    return {"workload": wname, "instances": len(ws),
+            "n_range": [min(w.graph.n for w in ws), max(w.graph.n for w in ws)],
+            "trials": sorted(set(w.trials for w in ws)), "anneal_steps": ws[0].steps, "variability": True,
+            "updates_per_step": sum(w.graph.n * w.trials * w.steps for w in ws)}
+
+
+# ------------------------------------------------------ oracle mean cut ----
+
+def _oracle_cuts(job):
+    """Whole-anneal cuts of one instance by the oracle (run in a spawned process)."""
+    import oracle
+    csr = oracle.Csr(job["n"], job["src"], job["dst"], job["w"])
+    tab = oracle.schedule(csr, job["c_min"], job["c_max"], job["steps"])
+    s0 = oracle.init_spins(job["n"], job["trials"], job["seed"], job["instance"])
+    out = oracle.anneal(csr, s0, tab, job["seed"], job["instance"], variability=job["var"])
+    return oracle.cut(job["src"], job["dst"], job["w"], out)
+
+
+def oracle_mean_cut_check(ws, gpu_cuts, count: int = 2):
+    """The "equal mean cut" condition: the oracle anneals every trial of the `count` smallest
+    instances (by n*T) on the same seeds and counters; their mean cut must be within 0.5 % of the
+    GPU's mean cut over the same trials.  Trials whose cuts differ are those where a float32/FP64
+    tie-band decision sent the trial down another path."""
+    order = sorted(range(len(ws)), key=lambda k: ws[k].graph.n * ws[k].trials)[:count]
+    jobs = [dict(n=ws[k].graph.n, src=ws[k].graph.src, dst=ws[k].graph.dst, w=ws[k].graph.w, trials=ws[k].trials,
+                 steps=ws[k].steps, c_min=ws[k].c_min, c_max=ws[k].c_max, seed=ws[k].seed,
+                 instance=ws[k].instance, var=ws[k].var) for k in order]
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        ref = pool.map(_oracle_cuts, jobs)
+    secs = time.perf_counter() - t0
+    gpu = [np.asarray(gpu_cuts[k])[:len(r)] for k, r in zip(order, ref)]
+    mg = float(np.mean(np.concatenate(gpu)))
+    mo = float(np.mean(np.concatenate(ref)))
+    rel = abs(mg - mo) / max(1.0, abs(mo))
+    return {"instances": [ws[k].name for k in order], "trials": [len(r) for r in ref],
+            "mean_cut_gpu": mg, "mean_cut_oracle": mo, "rel_diff": rel, "within_0p5pct": bool(rel <= 0.005),
+            "trials_identical": float(np.mean(np.concatenate([a == b for a, b in zip(gpu, ref)]))),
+            "oracle_seconds": secs}
+
+
+# ------------------------------------------------------ single instance ----
+
+def run_single(args, w, variant, kernel, dense, steps, warmup, e2e_reps, dist, world, local):
+    """Time whole anneals (+ exact cuts) of one instance: device time with CUDA events on the launching
+    stream, L2 flushed between timed anneals; the dominant kernel's roofline; the same anneal end to end
+    through the C ABI from host buffers."""
     import torch
     from paper_2601_14476_gb300 import pbit
-    rank, world, local, dist = _dist_setup()
+    g = w.graph
+    G = pbit.Graph.from_inputs(g, dense=dense)
+    T, S = w.trials, w.steps
+    stream = torch.cuda.current_stream()
+    spins = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+    cuts = torch.empty(T, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    params, keep = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
+                                    kernel=kernel, variability=w.var, stream=stream, **variant)
+    sub = max(1, variant.get("t_res", 0))  # updates per cycle and node-trial (timing model: sub-steps)
+
+    def one_run():
+        pbit.pbit_anneal(G.handle, params, None, spins)
+        pbit.pbit_cut_device(G.handle, spins, T, cuts, stream)
+
+    for _ in range(warmup):
+        one_run()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = pbit.pbit_launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()                     # L2 flushed between timed steps (not timed)
+            a.record(stream)
+            one_run()
+            b.record(stream)
+        torch.cuda.synchronize()
+    launches = pbit.pbit_launch_count() - launches0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    upd_run = getattr(w, "updates", g.n * T * S)  # the timing model counts the updates of due nodes only
+    value, ms_step = job_throughput(dist, upd_run, float(np.mean(ms)), world)
+
+    # dominant kernel: the anneal itself (one persistent launch for the dense path and the multi-step
+    # sparse form, one launch per step otherwise); its average launch duration from CUDA events on the
+    # launching stream
+    chosen = pbit.pbit_select_kernel(G.handle, kernel, T)
+    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    l0 = pbit.pbit_launch_count()
+    ka.record(stream)
+    pbit.pbit_anneal(G.handle, params, None, spins)
+    kb.record(stream)
+    torch.cuda.synchronize()
+    G.status()
+    anneal_ms = ka.elapsed_time(kb)
+    anneal_launches = pbit.pbit_launch_count() - l0
+    pk = peaks()
+    if chosen == pbit.KERNEL_DENSE:
+        # 2 n^2 T flops per step (algorithmic, unpadded); the anneal is one kernel timed alone, so the
+        # peak is the burst one: e4m3 tensor peak = 2 x the measured bf16 burst peak (nominal ratio)
+        flops = 2.0 * g.n * g.n * T * S
+        achieved = flops / (anneal_ms * 1e-3) / 1e12
+        peak = 2.0 * pk["bf16_tflops"]
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic_for("dense_persistent_kernel"),
+                    "kernel": "dense_persistent_kernel",
+                    "peak_source": f"{pk['source']} bf16 burst x2 (e4m3 nominal ratio)",
+                    "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
+    else:
+        kname = sparse_tile_kernel(g, T, anneal_launches, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
+        if variant:
+            kname = "sparse_variant_words_kernel" if T % 128 == 0 else "sparse_variant_kernel"
+        launches_main = S if kname in ("sparse_warp_kernel", "sparse_step_kernel") else 1
+        if variant:
+            launches_main = anneal_launches
+        per_launch_ms = anneal_ms / launches_main
+        mean_deg = 2.0 * g.m / g.n
+        # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
+        # (variants: plus their carried state and the timing model's copies, see variant_work)
+        if variant:
+            alg_bytes = variant_work(variant, g, T, S * sub)[1] / launches_main
+        else:
+            alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
+        achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"],
+                    "traffic": traffic_for(traffic_key(kname, variant)) if g.n == 20000 and T == 1024 else None,
+                    "kernel": kname, "peak_source": pk["source"],
+                    "per_launch": (f"variant bytes of the whole run (deg+2+state per update) / "
+                                   f"{launches_main} launches" if variant else
+                                   f"(deg+2) bytes x n*T updates per step; {launches_main} launches"),
+                    "note": "algorithmic gather bytes; the spin buffers largely stay in L2 (DRAM bytes in traffic)"}
+    roofline["kernel_ms_per_anneal"] = anneal_ms
+
+    # end to end through the C ABI from host buffers: graph upload, anneal, cut to host
+    e2e_ms = []
+    h2d = g.m * (4 + 4 + 1) + (3 * g.n * 4 if w.var else 0) + S * 4 + (4 * g.n if "nu_dev" in variant else 0)
+    d2h = T * 8
+    host_cuts = None
+    for it in range(0 if args.no_e2e else 1 + e2e_reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = pbit.Graph.from_inputs(g, dense=dense)
+        out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+        p2, keep2 = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
+                                     kernel=kernel, variability=w.var, stream=stream, **variant)
+        pbit.pbit_anneal(G2.handle, p2, None, out)
+        host_cuts = pbit.pbit_cut(G2.handle, out, T, stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        G2.close()
+        if it >= 1:
+            e2e_ms.append(dt * 1e3)
+    e2e_val = world * upd_run / (np.mean(e2e_ms) * 1e-3) if e2e_ms else None
+    if host_cuts is None:
+        host_cuts = cuts.cpu().numpy()
+    return {"value": value, "ms_per_anneal": ms_step, "roofline": roofline,
+            "kernel": {0: "auto", 1: "sparse", 2: "dense", 3: "resident"}[chosen],
+            "mean_cut": float(host_cuts.mean()), "launches": int(launches),
+            "e2e": {"value": e2e_val, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk.summary(), "updates_per_anneal": upd_run}
+
+
+# ---------------------------------------------------------------- batch ----
+
+def run_batch(args, ws, Gs, wname, dist, world, local):
+    """The batched persistent form (timed `args.steps` times) against the plain one-instance-per-launch
+    form of the same work on the same GPU; results must be identical per trial."""
+    import torch
+    from paper_2601_14476_gb300 import pbit
     pk = peaks()
     stream = torch.cuda.current_stream()
-    if args.config in ("batch", "sweep"):
-        if args.config == "batch":
-            ws = inputs.batch64(seed=1 + rank, steps=args.anneal_steps or 2000)
-            Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
-            wname = f"batch64_uneven_S{ws[0].steps}"
-        else:
-            ws = sweep_workloads(seed=1 + rank, steps=args.anneal_steps or 1000)
-            Gs = [pbit.Graph.from_inputs(ws[0].graph)] * len(ws)
-            wname = f"sweep{len(ws)}_torus100x200_T128_S{ws[0].steps}"
-        kws = [dict(trials=w.trials, steps=w.steps, seed=w.seed, instance=w.instance, variability=w.var,
-                    i0_min=w.c_min, i0_max=w.c_max) for w in ws]
-        upd_run = sum(w.graph.n * w.trials * w.steps for w in ws)
-        bytes_run = sum(w.graph.n * w.trials * w.steps * (2.0 * w.graph.m / w.graph.n + 2.0) for w in ws)
-        B0 = pbit.Batch(Gs, kws)
-        tuning = B0.autotune(stream)
-        B0.close()
-        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    kws = [dict(trials=w.trials, steps=w.steps, seed=w.seed, instance=w.instance, variability=w.var,
+                i0_min=w.c_min, i0_max=w.c_max) for w in ws]
+    upd_run = sum(w.graph.n * w.trials * w.steps for w in ws)
+    bytes_run = sum(w.graph.n * w.trials * w.steps * (2.0 * w.graph.m / w.graph.n + 2.0) for w in ws)
+    B0 = pbit.Batch(Gs, kws)
+    tuning = B0.autotune(stream)
+    B0.close()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-        def batched_run():
-            B = pbit.Batch(Gs, kws)
-            pbit.pbit_batch_set_tuning(B.handle, tuning["chunk_steps"], tuning["ctas_per_sm"])
-            return B
+    def batched_run():
+        B = pbit.Batch(Gs, kws)
+        pbit.pbit_batch_set_tuning(B.handle, tuning["chunk_steps"], tuning["ctas_per_sm"])
+        return B
 
-        for _ in range(args.warmup):
-            B = batched_run()
-            B.run(stream=stream)
+    for _ in range(args.warmup):
+        B = batched_run()
+        B.run(stream=stream)
+        torch.cuda.synchronize()
+        B.close()
+    if dist:
+        dist.barrier()
+    times = []
+    launches0 = pbit.pbit_launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            B = batched_run()          # instance setup is outside the timed region
+            flush.zero_()
             torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.run(stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+            batched_cuts = [B.cuts(k) for k in range(len(ws))]
             B.close()
-        if dist:
-            dist.barrier()
-        times = []
-        launches0 = pbit.pbit_launch_count()
-        with ClockSampler(local) as clk:
-            for _ in range(args.steps):
-                B = batched_run()          # instance setup is outside the timed region
-                flush.zero_()
-                torch.cuda.synchronize()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                B.run(stream=stream)
-                b.record(stream)
-                torch.cuda.synchronize()
-                times.append(a.elapsed_time(b))
-                batched_cuts = [B.cuts(k) for k in range(len(ws))]
-                B.close()
-        launches = pbit.pbit_launch_count() - launches0
-        value, ms = job_throughput(dist, upd_run, float(np.mean(times)), world)
-        # plain form: one instance after another, one launch per step (or one resident launch)
+    launches = pbit.pbit_launch_count() - launches0
+    value, ms = job_throughput(dist, upd_run, float(np.mean(times)), world)
+    # plain form: one instance after another through pbit_anneal (AUTO: the cluster-resident kernel for
+    # the small instances, the sparse path otherwise); one untimed pass builds the per-graph tables
+    outs = [torch.empty((w.graph.n, w.trials), dtype=torch.int8, device="cuda") for w in ws]
+    plist = [pbit.make_params(stream=stream, **kw) for kw in kws]
+    plain_ms_all = []
+    for it in range(1 + max(1, args.plain_reps)):
+        flush.zero_()
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        outs = [torch.empty((w.graph.n, w.trials), dtype=torch.int8, device="cuda") for w in ws]
         a.record(stream)
-        for G, w, o, kw in zip(Gs, ws, outs, kws):
-            p, keep = pbit.make_params(stream=stream, **kw)
+        for G, o, (p, keep) in zip(Gs, outs, plist):
             pbit.pbit_anneal(G.handle, p, None, o)
         b.record(stream)
         torch.cuda.synchronize()
-        plain_ms = a.elapsed_time(b)
-        plain_cuts = [G.cut(o) for G, o in zip(Gs, outs)]
-        same = all(np.array_equal(x, y) for x, y in zip(batched_cuts, plain_cuts))
-        mean_b = float(np.mean([c.mean() for c in batched_cuts]))
-        mean_p = float(np.mean([c.mean() for c in plain_cuts]))
-        # e2e: graphs from host arrays, batch setup, run, cuts back to host
+        if it >= 1:
+            plain_ms_all.append(a.elapsed_time(b))
+    plain_value, plain_ms = job_throughput(dist, upd_run, float(np.mean(plain_ms_all)), world)
+    plain_cuts = [G.cut(o) for G, o in zip(Gs, outs)]
+    same = all(np.array_equal(x, y) for x, y in zip(batched_cuts, plain_cuts))
+    # end to end: graphs from host arrays, batch setup, run, cuts back to host
+    e2e = []
+    for it in range(0 if args.no_e2e else 2):
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G2 = ([pbit.Graph.from_inputs(w.graph) for w in ws] if args.config == "batch"
+        G2 = ([pbit.Graph.from_inputs(w.graph) for w in ws] if wname.startswith("batch")
               else [pbit.Graph.from_inputs(ws[0].graph)] * len(ws))
         B2 = pbit.Batch(G2, kws)
         pbit.pbit_batch_set_tuning(B2.handle, tuning["chunk_steps"], tuning["ctas_per_sm"])
         B2.run(stream=stream)
         host_cuts = [B2.cuts(k) for k in range(len(ws))]
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
+        e2e.append(time.perf_counter() - t0)
         B2.close()
-        h2d = sum((w.graph.m * 9 if (args.config == "batch" or k == 0) else 0) + (12 * w.graph.n if w.var else 0)
-                  + 4 * w.steps for k, w in enumerate(ws))
-        d2h = sum(8 * w.trials for w in ws)
-        achieved = bytes_run / (ms * 1e-3) / 1e9
-        line = {
-            "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
-            "config": {"workload": wname, "instances": len(ws),
-                       "n_range": [min(w.graph.n for w in ws), max(w.graph.n for w in ws)],
-                       "trials": sorted(set(w.trials for w in ws)), "updates_per_step": upd_run,
-                       "tuning": tuning, "l2": "flushed between timed steps",
-                       "plain_value": world * upd_run / (plain_ms * 1e-3), "plain_ms": plain_ms,
-                       "batched_over_plain": plain_ms / ms, "cuts_identical_to_plain": bool(same),
-                       "mean_cut_batched": mean_b, "mean_cut_plain": mean_p},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / pk["hbm_gbs"], "traffic": batch_traffic(tuning, ws[0].steps) if args.config == "batch" else None,
-                         "kernel": "batch_chunk_kernel",
-                         "peak_source": pk["source"],
-                         "per_launch": "sum over instances of (deg+2) bytes x n*T updates per step"},
-            "cpu_baseline": None,
-            "e2e": {"value": world * upd_run / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": int(launches), "clocks": clk.summary(),
-        }
-        if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(multi_reference_workload(args.config), kind=args.config)
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        if dist:
-            dist.destroy_process_group()
-        return
+        for G in set(G2):
+            G.close()
+    one_graph = not wname.startswith("batch")
+    h2d = sum((w.graph.m * 9 if (not one_graph or k == 0) else 0) + (12 * w.graph.n if w.var else 0)
+              + 4 * w.steps for k, w in enumerate(ws))
+    d2h = sum(8 * w.trials for w in ws)
+    achieved = bytes_run / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"],
+                "traffic": batch_traffic(tuning, ws[0].steps) if wname.startswith("batch") else None,
+                "kernel": "batch_chunk_kernel", "peak_source": pk["source"],
+                "per_launch": "sum over instances of (deg+2) bytes x n*T updates per step, over the "
+                              "batched run's chunk launches",
+                "note": "algorithmic gather bytes; DRAM bytes of the whole run in traffic"}
+    return {"value": value, "ms": ms, "upd_run": upd_run, "tuning": tuning, "plain_value": plain_value,
+            "plain_ms": plain_ms, "batched_over_plain": plain_ms / ms, "cuts_identical_to_plain": bool(same),
+            "mean_cut_batched": float(np.mean([c.mean() for c in batched_cuts])),
+            "mean_cut_plain": float(np.mean([c.mean() for c in plain_cuts])),
+            "batched_cuts": batched_cuts, "roofline": roofline, "launches": int(launches),
+            "e2e": {"value": world * upd_run / float(np.mean(e2e)) if e2e else None, "unit": "spin-updates/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk.summary()}
 
-    # ---- serve: Poisson sweep
+
+# ---------------------------------------------------------------- serve ----
+
+def run_serve(args, rank, local):
+    """Poisson request streams through the continuous-batching server, one per arrival rate: p50/p99
+    latency from submission to result, and the aggregate spin-updates/s."""
+    from paper_2601_14476_gb300 import pbit
     rates = [float(r) for r in args.serve_rates.split(",")]
     # a pool of request graphs (n log-uniform in [800, 20000], G(n,3n) w=+1 or 3-NN RGG w=+-1) built
     # before the sweep; every request draws its own trials, steps, variability and seed
@@ -519,10 +687,10 @@ def bench_multi(args):
                 t_sub = time.perf_counter()
                 rid = pbit.pbit_server_submit(srv, G.handle, p)
                 pending[rid] = (T, w.graph.n * T * S, keep, t_sub)
-            # drain for up to 20 s; a request still unfinished then counts with its age so far as a
+            # drain for up to serve_drain s; a request still unfinished then counts with its age so far as a
             # lower bound of its latency (censored)
             lat, censored = [], 0
-            deadline = time.perf_counter() + 20.0
+            deadline = time.perf_counter() + args.serve_drain
             for rid, (T, u, keep, t_sub) in list(pending.items()):
                 left = deadline - time.perf_counter()
                 code = pbit.PBIT_PENDING
@@ -545,21 +713,157 @@ def bench_multi(args):
                           "p99_s": float(np.percentile(lat, 99)) if lat else None,
                           "updates_per_s": upd / wall, "peak_resident": st["peak_resident"]})
     launches = pbit.pbit_launch_count() - launches0
-    value = world * total_upd / total_wall
+    for G, _, _ in pool:
+        G.close()
+    return {"rates": rates, "window_s": args.serve_seconds, "drain_s": args.serve_drain, "sweep": sweep,
+            "saturation_updates_per_s": max(x["updates_per_s"] for x in sweep),
+            "aggregate_updates_per_s": total_upd / total_wall, "request_pool": len(pool),
+            "budget_bytes": 64 << 30, "max_slots": 64, "chunk_steps": 64,
+            "latency": "submit to result; unfinished after the drain enter with their age (censored)",
+            "launches": int(launches), "clocks": clk.summary()}
+
+
+# ------------------------------------------------------------- headline ----
+
+def bench_headline(args):
+    """The headline line: batched spin-updates/s on the uneven 64-instance batch, beside the plain form,
+    the oracle's mean cut, the serving sweep and the dense / sparse single-instance components."""
+    import torch
+    from paper_2601_14476_gb300 import pbit
+    rank, world, local, dist = _dist_setup()
+    ws = inputs.batch64(seed=1 + rank, steps=args.anneal_steps or 2000)
+    Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+    wname = f"batch64_uneven_S{ws[0].steps}"
+    b = run_batch(args, ws, Gs, wname, dist, world, local)
+    components = {}
+    if not args.no_components:
+        for name in ("dense", "sparse"):
+            w = workload(name)
+            w.instance = rank
+            r = run_single(args, w, {}, pbit.KERNEL_AUTO, name == "dense", steps=max(3, min(args.steps, 5)),
+                           warmup=3, e2e_reps=1, dist=dist, world=world, local=local)
+            components[name] = {"workload": w.name, "n": w.graph.n, "edges": w.graph.m, "trials": w.trials,
+                                "anneal_steps": w.steps, "value": r["value"], "unit": "spin-updates/s",
+                                "ms_per_anneal": r["ms_per_anneal"], "kernel": r["kernel"],
+                                "kernel_ms_per_anneal": r["roofline"]["kernel_ms_per_anneal"],
+                                "roofline": r["roofline"], "e2e": r["e2e"], "mean_cut": r["mean_cut"],
+                                "clocks": r["clocks"]}
+    serve = run_serve(args, rank, local) if not args.no_serve else None
+    if serve:
+        serve["served_over_plain"] = serve["saturation_updates_per_s"] / (b["plain_value"] / world)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    check = None if args.no_oracle_check else oracle_mean_cut_check(ws, b["batched_cuts"])
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(multi_reference_workload("batch"), kind="headline")
+    cfg = batch_config(ws, wname)
+    cfg.update({"l2": "flushed between timed steps", "tuning": b["tuning"],
+                "plain_value": b["plain_value"], "plain_ms": b["plain_ms"],
+                "plain_form": "each instance in turn through pbit_anneal (AUTO kernel)",
+                "batched_over_plain": b["batched_over_plain"], "cuts_identical_to_plain": b["cuts_identical_to_plain"],
+                "mean_cut_batched": b["mean_cut_batched"], "mean_cut_plain": b["mean_cut_plain"],
+                "oracle_mean_cut": check, "serve": serve, "components": components})
     line = {
-        "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
-        "steps": len(rates), "warmup": args.warmup, "ms_per_step": 1e3 * total_wall / max(1, len(rates)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
-        "config": {"workload": "poisson_serving", "rates": rates, "window_s": args.serve_seconds,
-                   "request_pool": len(pool), "sweep": sweep, "budget_bytes": 64 << 30, "max_slots": 64,
-                   "latency": "submit to result; unfinished after a 20 s drain enter with their age (censored)",
-                   "chunk_steps": 64, "l2": "inputs larger than L2 in aggregate"},
-        "roofline": None, "cpu_baseline": None,
-        "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
-        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "metric": "spin-updates/s", "value": b["value"], "unit": "spin-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic", "config": cfg,
+        "roofline": b["roofline"], "cpu_baseline": cb, "e2e": b["e2e"], "gpu_launches": b["launches"],
+        "clocks": b["clocks"],
     }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------- other configurations ----
+
+def bench_multi(args):
+    """config batch / sweep: the batched persistent form vs the plain form; config serve: the Poisson
+    serving sweep alone."""
+    import torch  # noqa: F401
+    from paper_2601_14476_gb300 import pbit
+    rank, world, local, dist = _dist_setup()
+    if args.config in ("batch", "sweep"):
+        if args.config == "batch":
+            ws = inputs.batch64(seed=1 + rank, steps=args.anneal_steps or 2000)
+            Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+            wname = f"batch64_uneven_S{ws[0].steps}"
+        else:
+            ws = sweep_workloads(seed=1 + rank, steps=args.anneal_steps or 1000)
+            Gs = [pbit.Graph.from_inputs(ws[0].graph)] * len(ws)
+            wname = f"sweep{len(ws)}_torus100x200_T128_S{ws[0].steps}"
+        b = run_batch(args, ws, Gs, wname, dist, world, local)
+        if rank == 0:
+            cfg = batch_config(ws, wname)
+            cfg.update({"tuning": b["tuning"], "l2": "flushed between timed steps", "plain_value": b["plain_value"],
+                        "plain_ms": b["plain_ms"], "batched_over_plain": b["batched_over_plain"],
+                        "cuts_identical_to_plain": b["cuts_identical_to_plain"],
+                        "mean_cut_batched": b["mean_cut_batched"], "mean_cut_plain": b["mean_cut_plain"]})
+            line = {"metric": "spin-updates/s", "value": b["value"], "unit": "spin-updates/s", "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic", "config": cfg,
+                    "roofline": b["roofline"], "cpu_baseline": None, "e2e": b["e2e"],
+                    "gpu_launches": b["launches"], "clocks": b["clocks"]}
+            if world == 1 and not args.no_cpu_baseline:
+                line["cpu_baseline"] = cpu_baseline(multi_reference_workload(args.config), kind=args.config)
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+    serve = run_serve(args, rank, local)
     if rank == 0:
+        line = {"metric": "spin-updates/s", "value": world * serve["aggregate_updates_per_s"], "unit": "spin-updates/s",
+                "n_gpus": world, "steps": len(serve["rates"]), "warmup": args.warmup,
+                "ms_per_step": 1e3 * args.serve_seconds, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
+                "config": {"workload": "poisson_serving", **{k: v for k, v in serve.items() if k != "clocks"},
+                           "l2": "inputs larger than L2 in aggregate"},
+                "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": world * serve["aggregate_updates_per_s"], "unit": "spin-updates/s",
+                        "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+                "gpu_launches": serve["launches"], "clocks": serve["clocks"]}
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def bench_one(args):
+    """A single-instance workload (dense, sparse, plain; optionally a pSA variant)."""
+    from paper_2601_14476_gb300 import pbit
+    w = workload(args.config)
+    if args.anneal_steps > 0:
+        w.steps = args.anneal_steps
+        w.name += f"_first{args.anneal_steps}steps"
+    variant = variant_args(args, w)
+    if args.impl == "reference":
+        return run_reference(args, w, variant)
+    rank, world, local, dist = _dist_setup()
+    # each rank anneals its own instance of the workload (weak scaling, no data-path collective)
+    w.instance = rank
+    kernel = {"auto": pbit.KERNEL_AUTO, "sparse": pbit.KERNEL_SPARSE, "dense": pbit.KERNEL_DENSE,
+              "resident": pbit.KERNEL_RESIDENT}[args.kernel]
+    r = run_single(args, w, variant, kernel, args.config == "dense", steps=args.steps, warmup=args.warmup,
+                   e2e_reps=args.steps, dist=dist, world=world, local=local)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(w, kind=args.config, variant=variant)
+    line = {
+        "metric": "spin-updates/s", "value": r["value"], "unit": "spin-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_anneal"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
+        "config": {**workload_config(w), "l2": "flushed between timed steps", "kernel": r["kernel"],
+                   "mean_cut": r["mean_cut"]},
+        "roofline": r["roofline"], "cpu_baseline": cb, "e2e": r["e2e"], "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -571,13 +875,19 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", default="dense", choices=["dense", "sparse", "plain", "batch", "serve", "sweep"])
-    ap.add_argument("--serve-seconds", type=float, default=5.0, help="arrival window per rate (serve config)")
+    ap.add_argument("--config", default="headline",
+                    choices=["headline", "dense", "sparse", "plain", "batch", "serve", "sweep"])
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate (serving)")
+    ap.add_argument("--serve-drain", type=float, default=15.0, help="longest wait for a rate's last results")
     ap.add_argument("--serve-rates", default="10,30,100,300,1000")
+    ap.add_argument("--plain-reps", type=int, default=2, help="timed passes of the plain form")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "sparse", "dense", "resident"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="headline: leave out the serving sweep")
+    ap.add_argument("--no-components", action="store_true", help="headline: leave out the dense/sparse lines")
+    ap.add_argument("--no-oracle-check", action="store_true", help="headline: leave out the oracle's mean cut")
     ap.add_argument("--anneal-steps", type=int, default=0,
                     help="shorten the schedule (profiling captures only; such a line is not a bench value)")
     ap.add_argument("--algorithm", default="psa", choices=["psa", "spsa", "tapsa"],
@@ -589,165 +899,17 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.config == "headline":
+        if args.impl == "reference":
+            ws = inputs.batch64(steps=args.anneal_steps or 2000)
+            return run_reference(args, multi_reference_workload("batch"),
+                                 config=batch_config(ws, f"batch64_uneven_S{ws[0].steps}"))
+        return bench_headline(args)
     if args.config in ("batch", "serve", "sweep"):
         if args.impl == "reference":
             return run_reference(args, multi_reference_workload(args.config))
         return bench_multi(args)
-    w = workload(args.config)
-    if args.anneal_steps > 0:
-        w.steps = args.anneal_steps
-        w.name += f"_first{args.anneal_steps}steps"
-    variant = variant_args(args, w)
-    if args.impl == "reference":
-        return run_reference(args, w, variant)
-
-    import torch
-    from paper_2601_14476_gb300 import pbit
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    # each rank anneals its own instance of the workload (weak scaling, no data-path collective)
-    w.instance = rank
-    kernel = {"auto": pbit.KERNEL_AUTO, "sparse": pbit.KERNEL_SPARSE, "dense": pbit.KERNEL_DENSE,
-              "resident": pbit.KERNEL_RESIDENT}[args.kernel]
-    g = w.graph
-    G = pbit.Graph.from_inputs(g, dense=(args.config == "dense"))
-    T, S = w.trials, w.steps
-    stream = torch.cuda.current_stream()
-    spins = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
-    cuts = torch.empty(T, dtype=torch.int64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    params, keep = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
-                                    kernel=kernel, variability=w.var, stream=stream, **variant)
-    sub = max(1, variant.get("t_res", 0))  # updates per cycle and node-trial (timing model: sub-steps)
-
-    def one_run():
-        pbit.pbit_anneal(G.handle, params, None, spins)
-        pbit.pbit_cut_device(G.handle, spins, T, cuts, stream)
-
-    for _ in range(args.warmup):
-        one_run()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = pbit.pbit_launch_count()
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        for a, b in ev:
-            flush.zero_()                     # L2 flushed between timed steps (not timed)
-            a.record(stream)
-            one_run()
-            b.record(stream)
-        torch.cuda.synchronize()
-    launches = pbit.pbit_launch_count() - launches0
-    ms = [a.elapsed_time(b) for a, b in ev]
-    upd_run = getattr(w, "updates", g.n * T * S)  # the timing model counts the updates of due nodes only
-    value, ms_step = job_throughput(dist, upd_run, float(np.mean(ms)), world)
-
-    # dominant kernel: the anneal itself (one persistent launch for the dense path, one launch per step
-    # otherwise); its average launch duration from CUDA events on the launching stream
-    chosen = pbit.pbit_select_kernel(G.handle, kernel, T)
-    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.zero_()
-    l0 = pbit.pbit_launch_count()
-    ka.record(stream)
-    pbit.pbit_anneal(G.handle, params, None, spins)
-    kb.record(stream)
-    torch.cuda.synchronize()
-    G.status()
-    anneal_ms = ka.elapsed_time(kb)
-    anneal_launches = pbit.pbit_launch_count() - l0
-    pk = peaks()
-    if chosen == pbit.KERNEL_DENSE:
-        # 2 n^2 T flops per step (algorithmic, unpadded), e4m3 tensor peak = 2 x the measured bf16 peak
-        launches_main = 1
-        flops = 2.0 * g.n * g.n * T * S
-        achieved = flops / (anneal_ms * 1e-3) / 1e12
-        peak = 2.0 * pk["bf16_tflops_sustained"]
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic_for("dense_persistent_kernel"),
-                    "kernel": "dense_persistent_kernel",
-                    "peak_source": f"{pk['source']} bf16 sustained x2 (e4m3 nominal ratio)",
-                    "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
-    else:
-        kname = sparse_tile_kernel(g, T, anneal_launches, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
-        if variant:
-            kname = "sparse_variant_words_kernel" if T % 128 == 0 else "sparse_variant_kernel"
-        launches_main = S if kname in ("sparse_warp_kernel", "sparse_step_kernel") else 1
-        if variant:
-            launches_main = anneal_launches
-        per_launch_ms = anneal_ms / launches_main
-        mean_deg = 2.0 * g.m / g.n
-        # algorithmic bytes per spin-update of the sparse gather: deg neighbour bytes + own + write
-        # (variants: plus their carried state and the timing model's copies, see variant_work)
-        if variant:
-            alg_bytes = variant_work(variant, g, T, S * sub)[1] / launches_main
-        else:
-            alg_bytes = g.n * T * (mean_deg + 2.0) * (S / launches_main)
-        achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / pk["hbm_gbs"],
-                    "traffic": traffic_for(traffic_key(kname, variant)) if g.n == 20000 and T == 1024 else None,
-                    "kernel": kname,
-                    "peak_source": pk["source"],
-                    "per_launch": (f"variant bytes of the whole run (deg+2+state per update) / "
-                                   f"{launches_main} launches" if variant else
-                                   f"(deg+2) bytes x n*T updates per step; {launches_main} launches")}
-    roofline["kernel_ms_per_anneal"] = anneal_ms
-
-    # end to end through the C ABI from host buffers: graph upload, anneal, cut to host
-    e2e_ms = []
-    h2d = g.m * (4 + 4 + 1) + (3 * g.n * 4 if w.var else 0) + S * 4 + (4 * g.n if "nu_dev" in variant else 0)
-    d2h = T * 8
-    for it in range(0 if args.no_e2e else 2 + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        G2 = pbit.Graph.from_inputs(g, dense=(args.config == "dense"))
-        out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
-        p2, keep2 = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance,
-                                     kernel=kernel, variability=w.var, stream=stream, **variant)
-        pbit.pbit_anneal(G2.handle, p2, None, out)
-        host_cuts = pbit.pbit_cut(G2.handle, out, T, stream)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        G2.close()
-        if it >= 2:
-            e2e_ms.append(dt * 1e3)
-    e2e_val = world * upd_run / (np.mean(e2e_ms) * 1e-3) if e2e_ms else None
-    if not e2e_ms:
-        host_cuts = cuts.cpu().numpy()
-
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-    cb = None
-    if not args.no_cpu_baseline and world == 1:
-        cb = cpu_baseline(w, kind=args.config, variant=variant)
-    line = {
-        "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic",
-        "config": {**workload_config(w), "l2": "flushed between timed steps",
-                   "kernel": {0: "auto", 1: "sparse", 2: "dense", 3: "resident"}[chosen],
-                   "mean_cut": float(host_cuts.mean())},
-        "roofline": roofline,
-        "cpu_baseline": cb,
-        "e2e": {"value": e2e_val, "unit": "spin-updates/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-    }
-    print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    return bench_one(args)
 
 
 if __name__ == "__main__":

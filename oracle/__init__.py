@@ -65,8 +65,11 @@ def _lib():
             lib.orc_step_sampled.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, u64, u32, u32, C.c_float, P,
                                              i64, P, P, P, P]
             lib.orc_init_spins.argtypes = [i32, i32, u64, u32, P]
+            lib.orc_init_spins_trials.argtypes = [i32, i32, i32, u64, u32, P]
             lib.orc_anneal.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, u64, u32, P, i32, i32, P]
             lib.orc_anneal.restype = C.c_int
+            lib.orc_anneal_trials.argtypes = [i32, P, P, P, P, i32, i32, P, P, P, i32, u64, u32, P, i32, i32, P]
+            lib.orc_anneal_trials.restype = C.c_int
             lib.orc_timing_period.argtypes = [i32, C.c_float]
             lib.orc_timing_period.restype = i32
             lib.orc_step_variant.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, u64, u32, i32, f64, i32, i32, P,
@@ -165,9 +168,10 @@ def bruteforce_maxcut(n, src, dst, w):
     return int(val), best
 
 
-def init_spins(n: int, T: int, seed: int, instance: int = 0) -> np.ndarray:
+def init_spins(n: int, T: int, seed: int, instance: int = 0, trial_base: int = 0) -> np.ndarray:
+    """Initial state of trials trial_base .. trial_base + T - 1 (column t is trial trial_base + t)."""
     out = np.zeros((n, T), np.int8)
-    _lib().orc_init_spins(int(n), int(T), seed, instance, _p(out))
+    _lib().orc_init_spins_trials(int(n), int(T), int(trial_base), seed, instance, _p(out))
     return out
 
 
@@ -204,15 +208,18 @@ def step_sampled(csr: Csr, sigma, nodes, trials, step_idx: int, I0: float, seed:
 
 
 def anneal(csr: Csr, sigma0, table, seed: int, instance: int = 0, variability=None, h=None,
-           offset_mode: int = OFFSET_SCALED, step_begin: int = 0, step_end: int | None = None) -> np.ndarray:
+           offset_mode: int = OFFSET_SCALED, step_begin: int = 0, step_end: int | None = None,
+           trial_base: int = 0) -> np.ndarray:
+    """Schedule steps [step_begin, step_end) of the trials whose columns sigma0 holds: column t is
+    trial trial_base + t (the trials are independent, so any range of them can run alone)."""
     sigma = np.array(sigma0, dtype=np.int8, order="C", copy=True)
     T = sigma.shape[1]
     table = _c(table, np.float32)
     if step_end is None:
         step_end = len(table)
     lam, dlt, pu = _var(variability)
-    rc = _lib().orc_anneal(*csr.args(), _p(_c(h, np.int32)), T, _p(lam), _p(dlt), _p(pu), offset_mode, seed,
-                           instance, _p(table), int(step_begin), int(step_end), _p(sigma))
+    rc = _lib().orc_anneal_trials(*csr.args(), _p(_c(h, np.int32)), T, int(trial_base), _p(lam), _p(dlt), _p(pu),
+                                  offset_mode, seed, instance, _p(table), int(step_begin), int(step_end), _p(sigma))
     if rc != 0:
         raise MemoryError("oracle anneal failed")
     return sigma

@@ -272,6 +272,7 @@ typedef struct {
     int32_t offset_mode;
     uint64_t seed;
     uint32_t instance;
+    int32_t trial_base;      /* global index of column 0: column t is trial trial_base + t */
 } orc_problem;
 
 /* x for one node given its exact field D and the current I0. */
@@ -295,7 +296,7 @@ static int8_t orc_next(const orc_problem* P, const int8_t* sigma, int32_t i, int
     for (int32_t k = P->row_ptr[i]; k < P->row_ptr[i + 1]; ++k)
         D += (int64_t)P->J[k] * sigma[(int64_t)P->col[k] * P->T + t];
     double x = orc_input(P, i, D, I0);
-    orc_draw dr = orc_draw_for(P->seed, P->instance, i, step, t);
+    orc_draw dr = orc_draw_for(P->seed, P->instance, i, step, P->trial_base + t);
     double g = tanh(x) - dr.r;
     int8_t cand = g > 0.0 ? 1 : -1;
     double p = P->p_update ? (double)P->p_update[i] : 1.0;
@@ -310,7 +311,18 @@ static void orc_problem_init(orc_problem* P, int32_t n, const int32_t* row_ptr, 
                              const float* p_update, int32_t offset_mode, uint64_t seed, uint32_t instance) {
     P->n = n; P->row_ptr = row_ptr; P->col = col; P->J = J; P->h = h; P->T = T;
     P->lambda = lambda; P->delta = delta; P->p_update = p_update; P->offset_mode = offset_mode;
-    P->seed = seed; P->instance = instance;
+    P->seed = seed; P->instance = instance; P->trial_base = 0;
+}
+
+/* One Jacobi step of the columns of sigma_in (trials trial_base .. trial_base+T-1). */
+static void orc_step_cols(const orc_problem* P, uint32_t step, float I0, const int8_t* sigma_in, int8_t* sigma_out,
+                          double* gap) {
+    for (int32_t i = 0; i < P->n; ++i)
+        for (int32_t t = 0; t < P->T; ++t) {
+            double g;
+            sigma_out[(int64_t)i * P->T + t] = orc_next(P, sigma_in, i, t, step, I0, &g, NULL);
+            if (gap) gap[(int64_t)i * P->T + t] = g;
+        }
 }
 
 /* sigma_out = one Jacobi step of sigma_in at schedule index `step` with I0. */
@@ -320,12 +332,7 @@ void orc_step(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8_
               uint32_t instance, uint32_t step, float I0, const int8_t* sigma_in, int8_t* sigma_out, double* gap) {
     orc_problem P;
     orc_problem_init(&P, n, row_ptr, col, J, h, T, lambda, delta, p_update, offset_mode, seed, instance);
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t t = 0; t < T; ++t) {
-            double g;
-            sigma_out[(int64_t)i * T + t] = orc_next(&P, sigma_in, i, t, step, I0, &g, NULL);
-            if (gap) gap[(int64_t)i * T + t] = g;
-        }
+    orc_step_cols(&P, step, I0, sigma_in, sigma_out, gap);
 }
 
 /* The same step, evaluated only at the listed (node, trial) pairs.          */
@@ -343,30 +350,48 @@ void orc_step_sampled(int32_t n, const int32_t* row_ptr, const int32_t* col, con
     }
 }
 
-/* Initial state: +1 iff the step-0xFFFFFFFF draw has r < 0.                 */
-void orc_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* sigma) {
+/* Initial state of trials trial_base .. trial_base+T-1 (column t is trial   */
+/* trial_base + t): +1 iff the step-0xFFFFFFFF draw has r < 0.               */
+void orc_init_spins_trials(int32_t n, int32_t T, int32_t trial_base, uint64_t seed, uint32_t instance,
+                           int8_t* sigma) {
     for (int32_t i = 0; i < n; ++i)
         for (int32_t t = 0; t < T; ++t) {
-            orc_draw d = orc_draw_for(seed, instance, i, 0xFFFFFFFFu, t);
+            orc_draw d = orc_draw_for(seed, instance, i, 0xFFFFFFFFu, trial_base + t);
             sigma[(int64_t)i * T + t] = d.r < 0.0 ? 1 : -1;
         }
 }
 
-/* Full anneal over schedule steps [step_begin, step_end) of `table`.        */
+void orc_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* sigma) {
+    orc_init_spins_trials(n, T, 0, seed, instance, sigma);
+}
+
+/* Full anneal over schedule steps [step_begin, step_end) of `table` for the */
+/* trials trial_base .. trial_base+T-1 (every trial is independent, so a    */
+/* range of columns equals those columns of a run over all trials).         */
 /* sigma holds the start state on entry and the final state on return.       */
-int orc_anneal(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8_t* J, const int32_t* h, int32_t T,
-               const float* lambda, const float* delta, const float* p_update, int32_t offset_mode, uint64_t seed,
-               uint32_t instance, const float* table, int32_t step_begin, int32_t step_end, int8_t* sigma) {
+int orc_anneal_trials(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8_t* J, const int32_t* h,
+                      int32_t T, int32_t trial_base, const float* lambda, const float* delta, const float* p_update,
+                      int32_t offset_mode, uint64_t seed, uint32_t instance, const float* table, int32_t step_begin,
+                      int32_t step_end, int8_t* sigma) {
     int64_t cells = (int64_t)n * T;
     int8_t* next = (int8_t*)malloc((size_t)cells);
     if (!next) return ORC_E_NOMEM;
+    orc_problem P;
+    orc_problem_init(&P, n, row_ptr, col, J, h, T, lambda, delta, p_update, offset_mode, seed, instance);
+    P.trial_base = trial_base;
     for (int32_t s = step_begin; s < step_end; ++s) {
-        orc_step(n, row_ptr, col, J, h, T, lambda, delta, p_update, offset_mode, seed, instance, (uint32_t)s,
-                 table[s], sigma, next, NULL);
+        orc_step_cols(&P, (uint32_t)s, table[s], sigma, next, NULL);
         memcpy(sigma, next, (size_t)cells);
     }
     free(next);
     return ORC_OK;
+}
+
+int orc_anneal(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8_t* J, const int32_t* h, int32_t T,
+               const float* lambda, const float* delta, const float* p_update, int32_t offset_mode, uint64_t seed,
+               uint32_t instance, const float* table, int32_t step_begin, int32_t step_end, int8_t* sigma) {
+    return orc_anneal_trials(n, row_ptr, col, J, h, T, 0, lambda, delta, p_update, offset_mode, seed, instance,
+                             table, step_begin, step_end, sigma);
 }
 
 /* ------------------------------------------------------------------ */

@@ -42,11 +42,12 @@ def test_variant_work_without_timing_is_every_node_every_step():
 
 
 def test_traffic_table_entries():
-    """Each captured DRAM figure names an existing summary and is reported only while its kernel's
-    sources hash as they did at the capture (else null)."""
+    """Each captured DRAM figure is reported only while its kernel's sources hash as they did at the
+    capture (else null), and every source it hashes exists."""
     for key, entry in bench.TRAFFIC.items():
         assert bench.traffic_for(key) in (entry["bytes"], None), key
-        assert os.path.exists(os.path.join(bench.ROOT, entry["capture"])), key
+        for f in entry["files"]:
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_2601_14476_gb300", "csrc", f)), (key, f)
     assert bench.traffic_key("sparse_variant_words_kernel", {"algorithm": pbit.ALG_SPSA}) in bench.TRAFFIC
     assert bench.traffic_key("sparse_variant_words_kernel", {"algorithm": pbit.ALG_PSA, "t_res": 10}) is None
     assert bench.traffic_for(None) is None

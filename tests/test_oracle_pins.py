@@ -388,3 +388,40 @@ def test_anneal_resume_identity():
     half = oracle.anneal(csr, s0, tab, seed=1, step_end=20)
     rest = oracle.anneal(csr, half, tab, seed=1, step_begin=20)
     assert np.array_equal(full, rest)
+
+
+def test_init_spins_rule_against_triton_philox():
+    """The initial state (reading: +1 iff the step-0xFFFFFFFF draw has r < 0) pinned to Triton's
+    independent Philox: r = (2k + 1 - 2^24) / 2^24 with k the top 24 bits of the r word, so r < 0
+    exactly when that word's top bit is 0."""
+    pytest.importorskip("triton")
+    seed, instance = 0x1234_5678_9ABC, 5
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    pairs = [(i, t) for i in (0, 1, 7, 40) for t in range(6)]
+    cases = [([i, 0xFFFFFFFF, t >> 1, instance], key) for i, t in pairs]
+    script = os.path.join(ROOT, "tests", "golden", "triton_philox.py")
+    res = subprocess.run([sys.executable, script], input=json.dumps(cases), capture_output=True, text=True,
+                         env=dict(os.environ, TRITON_INTERPRET="1"), timeout=600)
+    if res.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {res.stderr[-300:]}")
+    words = json.loads(res.stdout)
+    s = oracle.init_spins(41, 6, seed, instance)
+    for (i, t), w in zip(pairs, words):
+        want = 1 if (w[2 * (t & 1)] >> 31) == 0 else -1
+        assert s[i, t] == want, (i, t)
+
+
+def test_trial_range_equals_columns_of_the_full_run():
+    """Trials are independent: annealing trials [b, b+k) alone (initial state and Philox counters of
+    their global indices) gives exactly those columns of the run over all trials."""
+    g = _small_graph(60, 200, 8)
+    csr = oracle.Csr(g.n, g.src, g.dst, g.w)
+    tab = oracle.schedule(csr, 0.1, 10.0, 40)
+    var = inputs.variability(g.n, 8)
+    T = 12
+    full = oracle.anneal(csr, oracle.init_spins(g.n, T, 3, 2), tab, 3, 2, variability=var)
+    for b, k in ((0, 2), (3, 4), (10, 2), (11, 1)):
+        s0 = oracle.init_spins(g.n, k, 3, 2, trial_base=b)
+        assert np.array_equal(s0, oracle.init_spins(g.n, T, 3, 2)[:, b:b + k])
+        part = oracle.anneal(csr, s0, tab, 3, 2, variability=var, trial_base=b)
+        assert np.array_equal(part, full[:, b:b + k]), (b, k)
