@@ -321,7 +321,7 @@ def run_reference(args, w, variant=None, config=None):
             t_all.append(b["value"])
             base = b
     val = float(np.mean(t_all))
-    upd_run = getattr(w, "updates", w.graph.n * w.trials * w.steps)
+    upd_run = (config or {}).get("updates_per_step") or getattr(w, "updates", w.graph.n * w.trials * w.steps)
     line = {"impl": "reference", "metric": "spin-updates/s", "value": val, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * upd_run / val, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -391,16 +391,6 @@ def batch_config(ws, wname):
 
 # ------------------------------------------------------ oracle mean cut ----
 
-def _oracle_cuts(job):
-    """Whole-anneal cuts of one instance by the oracle (run in a spawned process)."""
-    import oracle
-    csr = oracle.Csr(job["n"], job["src"], job["dst"], job["w"])
-    tab = oracle.schedule(csr, job["c_min"], job["c_max"], job["steps"])
-    s0 = oracle.init_spins(job["n"], job["trials"], job["seed"], job["instance"])
-    out = oracle.anneal(csr, s0, tab, job["seed"], job["instance"], variability=job["var"])
-    return oracle.cut(job["src"], job["dst"], job["w"], out)
-
-
 def oracle_mean_cut_check(ws, gpu_cuts, count: int = 2):
     """The "equal mean cut" condition: the oracle anneals every trial of the `count` smallest
     instances (by n*T) on the same seeds and counters; their mean cut must be within 0.5 % of the
@@ -411,9 +401,11 @@ def oracle_mean_cut_check(ws, gpu_cuts, count: int = 2):
                  steps=ws[k].steps, c_min=ws[k].c_min, c_max=ws[k].c_max, seed=ws[k].seed,
                  instance=ws[k].instance, var=ws[k].var) for k in order]
     import multiprocessing as mp
+
+    import oracle
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
-        ref = pool.map(_oracle_cuts, jobs)
+        ref = pool.map(oracle.anneal_cuts, jobs)
     secs = time.perf_counter() - t0
     gpu = [np.asarray(gpu_cuts[k])[:len(r)] for k, r in zip(order, ref)]
     mg = float(np.mean(np.concatenate(gpu)))

@@ -225,6 +225,18 @@ def anneal(csr: Csr, sigma0, table, seed: int, instance: int = 0, variability=No
     return sigma
 
 
+def anneal_cuts(job: dict) -> np.ndarray:
+    """Final cuts of a whole anneal of trials [base, base + trials) of one instance, from a picklable job
+    (keys n, src, dst, w, trials, steps, c_min, c_max, seed, instance, var, optional base), so that a
+    spawned process pool can share out the trials of a large instance."""
+    csr = Csr(job["n"], job["src"], job["dst"], job["w"])
+    tab = schedule(csr, job["c_min"], job["c_max"], job["steps"])
+    base = int(job.get("base", 0))
+    s0 = init_spins(job["n"], job["trials"], job["seed"], job["instance"], trial_base=base)
+    out = anneal(csr, s0, tab, job["seed"], job["instance"], variability=job["var"], trial_base=base)
+    return cut(job["src"], job["dst"], job["w"], out)
+
+
 def timing_period(t_res: int, nu_dev: float) -> int:
     return int(_lib().orc_timing_period(int(t_res), float(nu_dev)))
 

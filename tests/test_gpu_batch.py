@@ -60,20 +60,35 @@ def test_batch_chunking_and_autotune_do_not_change_results():
 
 
 def test_batch_resume_from_given_state_matches_oracle():
+    """A batch instance resumed from a given state (step_begin 25), advanced one step per chunk: each
+    step against the oracle from the batch's own state, every differing decision inside the tie band
+    and at most one in the sample; then the whole range in one run equals the stepped run."""
     g = inputs.rgg_knn(600, 3, 3, "pm1")
     var = inputs.variability(g.n, 3)
     G = pbit.Graph.from_inputs(g)
     csr = oracle.Csr(g.n, g.src, g.dst, g.w)
     T, S = 32, 40
     start = inputs.random_spins(g.n, T, 5)
+    tab = oracle.schedule(csr, 0.1, 10.0, S)
     B = pbit.Batch([G], [dict(trials=T, steps=S, step_begin=25, seed=4, variability=var)])
     pbit.pbit_batch_set_spins(B.handle, 0, torch.from_numpy(start).cuda())
-    B.run(chunk_steps=8)
-    got = B.spins(0).cpu().numpy()
-    tab = oracle.schedule(csr, 0.1, 10.0, S)
-    want = oracle.anneal(csr, start, tab, 4, 0, variability=var, step_begin=25)
-    # decisions may differ only inside the 1e-6 tie band; over 15 steps x 19200 decisions none is expected
-    assert (got != want).mean() < 1e-3
+    state = start
+    mis = dec = 0
+    for t in range(25, S):
+        B.run(chunk_steps=1, max_chunks=1)
+        assert B.progress(0) == t + 1
+        got = B.spins(0).cpu().numpy()
+        want, gap = oracle.step(csr, state, t, tab[t], 4, 0, variability=var, want_gap=True)
+        bad = got != want
+        assert not bad.any() or np.abs(gap[bad]).max() < 1e-6, t
+        mis += int(bad.sum())
+        dec += bad.size
+        state = got
+    assert mis <= max(1, int(1e-6 * dec)), (mis, dec)
+    W = pbit.Batch([G], [dict(trials=T, steps=S, step_begin=25, seed=4, variability=var)])
+    pbit.pbit_batch_set_spins(W.handle, 0, torch.from_numpy(start).cuda())
+    W.run(chunk_steps=8)
+    assert np.array_equal(W.spins(0).cpu().numpy(), state)
 
 
 def test_batch64_smallest_instances_match_oracle():

@@ -87,3 +87,35 @@ def test_server_overlap_and_budget():
         assert ei.value.code == pbit.PBIT_E_BUDGET
     finally:
         pbit.pbit_server_destroy(srv)
+
+
+def test_served_request_matches_oracle_in_the_mix():
+    """A request served among others (different sizes, trial counts and lengths, admitted together so
+    their chunks share launches) against the oracle's whole anneal on the same seed and instance:
+    per-trial cuts equal except trials a tie-band decision diverged, mean cut within 0.5 %."""
+    import oracle
+    target = inputs.Workload("target", inputs.rgg_knn(900, 21, 3, "pm1"), 32, 1000, 0.1, 10.0,
+                             inputs.variability(900, 21), 11, 3)
+    others = _requests(seed=4, k=3)
+    ws = [others[0], target, others[1], others[2]]
+    Gs = [pbit.Graph.from_inputs(w.graph) for w in ws]
+    srv = pbit.pbit_server_create(8 << 30, 16, 32)
+    try:
+        keep, ids = [], []
+        for G, w in zip(Gs, ws):
+            p, k = pbit.make_params(w.trials, w.steps, seed=w.seed, instance=w.instance, variability=w.var,
+                                    i0_min=w.c_min, i0_max=w.c_max)
+            keep.append((p, k))
+            ids.append(pbit.pbit_server_submit(srv, G.handle, p))
+        res = [pbit.pbit_server_wait(srv, rid, w.trials, timeout_s=300) for rid, w in zip(ids, ws)]
+        assert all(r[0] == pbit.PBIT_OK for r in res)
+        assert pbit.pbit_server_stats(srv)["peak_resident"] >= 2
+    finally:
+        pbit.pbit_server_destroy(srv)
+    got = res[1][1]
+    g = target.graph
+    ref = oracle.anneal_cuts(dict(n=g.n, src=g.src, dst=g.dst, w=g.w, trials=target.trials, steps=target.steps,
+                                  c_min=target.c_min, c_max=target.c_max, seed=target.seed,
+                                  instance=target.instance, var=target.var))
+    assert (got == ref).mean() >= 0.75, (got, ref)
+    assert abs(got.mean() - ref.mean()) <= 0.005 * ref.mean()

@@ -100,6 +100,12 @@ def _lockstep(g, T, steps, var, kernel, seed=11, instance=3, mode=pbit.OFFSET_SC
     return decisions, mismatches, worst
 
 
+def _few(mis, dec):
+    """Band mismatches allowed in a lockstep sample: fewer than 1e-6 of its decisions, and at most one
+    in a sample of under 1e6 decisions (the rate itself is checked over 1.5e7 decisions below)."""
+    return mis <= max(1, int(1e-6 * dec))
+
+
 @pytest.mark.parametrize("kernel", [pbit.KERNEL_SPARSE, pbit.KERNEL_RESIDENT])
 @pytest.mark.parametrize("mode", [pbit.OFFSET_SCALED, pbit.OFFSET_LISTING, pbit.OFFSET_EQUATION])
 def test_lockstep_decisions(kernel, mode):
@@ -107,7 +113,7 @@ def test_lockstep_decisions(kernel, mode):
     var = inputs.variability(g.n, 2, s_intensity=0.3, s_offset=0.3)
     dec, mis, worst = _lockstep(g, 32, 30, var, kernel, mode=mode)
     assert mis == 0 or worst < BAND, (mis, worst)
-    assert mis <= max(1, dec * 1e-6) * 3
+    assert _few(mis, dec), (mis, dec)
 
 
 @pytest.mark.parametrize("T", [1, 3, 16, 20])
@@ -116,6 +122,7 @@ def test_lockstep_ragged_trials(T):
     var = inputs.variability(g.n, 7)
     dec, mis, worst = _lockstep(g, T, 12, var, pbit.KERNEL_SPARSE)
     assert mis == 0 or worst < BAND
+    assert _few(mis, dec), (mis, dec)
 
 
 def test_resident_equals_sparse_full_run():
@@ -162,20 +169,66 @@ def test_hold_and_zero_edge_graph():
         E.anneal(64, 5, seed=1)
 
 
-def test_full_run_matches_oracle_mean_cut():
-    """Plain G(800,19176) workload: per-trial cuts equal the oracle's except trials a near-tie diverged."""
+def _explain_divergence(G, csr, w, trial, seg_begin, seg_end, tab):
+    """Step the GPU one step at a time from its own state at seg_begin (the resume form) and the oracle
+    beside it: every differing decision must lie in the tie band, and `trial` must take at least one
+    such decision in the segment.  Returns the number of band decisions of `trial`."""
+    g = w.graph
+    state = _host(G.anneal(w.trials, w.steps, step_end=seg_begin, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed,
+                           instance=w.instance, variability=w.var)) if seg_begin else \
+        oracle.init_spins(g.n, w.trials, w.seed, w.instance)
+    hits = 0
+    for t in range(seg_begin, seg_end):
+        d_in = _dev(state)
+        d_out = torch.empty_like(d_in)
+        p, keep = pbit.make_params(w.trials, w.steps, step_begin=t, step_end=t + 1, i0_min=w.c_min,
+                                   i0_max=w.c_max, seed=w.seed, instance=w.instance, variability=w.var)
+        pbit.pbit_anneal(G.handle, p, d_in, d_out)
+        gpu = _host(d_out)
+        want, gap = oracle.step(csr, state, t, tab[t], w.seed, w.instance, variability=w.var, want_gap=True)
+        bad = gpu != want
+        assert not bad.any() or np.abs(gap[bad]).max() < BAND, t
+        hits += int(bad[:, trial].sum())
+        state = gpu
+    return hits
+
+
+def test_plain_workload_energy_trace_matches_oracle():
+    """Plain G(800, 19176) workload (w = +1, ideal p-bits, 16 trials, 1000 steps).  Its final cut is 0
+    on both sides (synchronous pSA falls into the all-+1 / all--1 two-cycle), so the mean cut pins
+    nothing; the path there does.  The energy every 10 steps (pbit_anneal_trace) must equal the
+    oracle's energy of its own states at the same steps, and the final spins of the bench's launch
+    form (one resident launch) must equal the oracle's element by element, for every trial whose path
+    no tie-band decision changed; a trial that departs must be explained by a band decision in the
+    segment where its trace first differs."""
     w = inputs.plain_er800()
     g = w.graph
     csr = oracle.Csr(g.n, g.src, g.dst, g.w)
     tab = oracle.schedule(csr, w.c_min, w.c_max, w.steps)
     G = pbit.Graph.from_inputs(g)
-    out = G.anneal(w.trials, w.steps, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed)
-    gpu_cut = G.cut(out)
-    ref = oracle.anneal(csr, oracle.init_spins(g.n, w.trials, w.seed), tab, w.seed)
-    ref_cut = oracle.cut(g.src, g.dst, g.w, ref)
-    same = (gpu_cut == ref_cut).mean()
-    assert same >= 0.75, (gpu_cut, ref_cut)
-    assert abs(gpu_cut.mean() - ref_cut.mean()) <= 0.005 * max(1.0, abs(ref_cut.mean())) or same == 1.0
+    T, S, every = w.trials, w.steps, 10
+    whole = _host(G.anneal(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance))
+    trace = torch.zeros((S // every, T), dtype=torch.int64, device="cuda")
+    out = torch.empty((g.n, T), dtype=torch.int8, device="cuda")
+    p, keep = pbit.make_params(T, S, i0_min=w.c_min, i0_max=w.c_max, seed=w.seed, instance=w.instance)
+    pbit.pbit_anneal_trace(G.handle, p, None, out, every, 0, trace)
+    tr = _host(trace)
+    assert np.array_equal(_host(out), whole)  # segmented run = one launch
+    state = oracle.init_spins(g.n, T, w.seed, w.instance)
+    ref = np.zeros_like(tr)
+    for j in range(S // every):
+        state = oracle.anneal(csr, state, tab, w.seed, w.instance, step_begin=j * every, step_end=(j + 1) * every)
+        ref[j] = oracle.energy(csr, state)
+    # the trace is not trivial: energies change along the anneal and differ between trials
+    assert len(np.unique(tr[:20])) > 20 and np.ptp(tr[5]) > 0
+    diverged = [t for t in range(T) if not (np.array_equal(tr[:, t], ref[:, t])
+                                            and np.array_equal(whole[:, t], state[:, t]))]
+    assert len(diverged) <= 2, diverged
+    for t in diverged:
+        rows = np.nonzero(tr[:, t] != ref[:, t])[0]
+        j = int(rows[0]) if len(rows) else S // every - 1
+        assert _explain_divergence(G, csr, w, t, j * every, (j + 1) * every, tab) >= 1, t
+    assert np.array_equal(G.cut(_dev(whole)), oracle.cut(g.src, g.dst, g.w, whole))
 
 
 def test_full_size_torus_sampled():
