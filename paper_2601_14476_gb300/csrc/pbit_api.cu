@@ -79,6 +79,7 @@ static void release(Graph* g) {
     cudaFree(g->J);
     cudaFree(g->h);
     cudaFree(g->dense.J_e4m3);
+    cudaFree(g->dense4.J4);
     cudaFree(g->err);
     cudaFree(g->wabs);
     cudaFree(g->tab_off);
@@ -114,6 +115,11 @@ struct CallBuffers {
     }
 };
 
+// Either dense kernel can run T trials on this graph: the cluster-resident FP4 kernel or the e4m3 one.
+static bool any_dense_ok(const Graph& g, int32_t T, std::string* why) {
+    return dense4_shape_ok(g, T) || dense_shape_ok(g, T, why);
+}
+
 // Resolve PBIT_KERNEL_AUTO and check a forced kernel against the shape.
 static pbit_status select_kernel(const Graph& g, int requested, int32_t T, int* out, bool variant = false) {
     std::string why;
@@ -123,12 +129,12 @@ static pbit_status select_kernel(const Graph& g, int requested, int32_t T, int* 
         *out = PBIT_KERNEL_SPARSE;
         return PBIT_OK;
     }
-    if (requested == PBIT_KERNEL_DENSE && !dense_shape_ok(g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
+    if (requested == PBIT_KERNEL_DENSE && !any_dense_ok(g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
     if (requested == PBIT_KERNEL_RESIDENT && !resident_fits(g, T))
         return fail(PBIT_E_UNSUPPORTED, "anneal: n*T too large for the shared-memory resident kernel");
     int k = requested;
     if (k == PBIT_KERNEL_AUTO) {
-        if (dense_shape_ok(g, T, nullptr))
+        if (any_dense_ok(g, T, nullptr))
             k = PBIT_KERNEL_DENSE;
         else
             k = resident_preferred(g, T) ? PBIT_KERNEL_RESIDENT : PBIT_KERNEL_SPARSE;
@@ -381,6 +387,7 @@ pbit_status pbit_graph_create(int32_t n, int64_t n_edges, const int32_t* src, co
         }
     }
     if ((flags & PBIT_GRAPH_DENSE) && (st = build_dense_operand(*g)) != PBIT_OK) goto err;
+    if ((flags & PBIT_GRAPH_DENSE) && (st = build_dense4_operand(*g)) != PBIT_OK) goto err;
     *out = g.release();
     return PBIT_OK;
 err:
@@ -624,7 +631,17 @@ pbit_status pbit_anneal(pbit_graph g, const pbit_anneal_params* p, const int8_t*
         PBIT_CUDA_TRY(launch_resident_anneal(a, b, e, g->unit_weights && g->max_degree <= 127, s));
         return PBIT_OK;
     }
+    if (kernel == PBIT_KERNEL_DENSE && dense4_shape_ok(*g, T)) {
+        // cluster-resident FP4 kernel: the whole step range in one launch, int8 in and out
+        uint8_t* b0 = nullptr;
+        if ((st = cb.alloc(&b0, dense4_spin_bytes(*g, T))) != PBIT_OK) return st;
+        const cudaError_t de = launch_dense4(*g, a, cur, spins_out, nullptr, b0, b, e, s);
+        if (de == cudaSuccess) return PBIT_OK;
+        if (de != cudaErrorNotSupported) return cuda_fail(de, "dense fp4 cluster launch");
+    }
     if (kernel == PBIT_KERNEL_DENSE) {
+        std::string why;
+        if (!dense_shape_ok(*g, T, &why)) return fail(PBIT_E_UNSUPPORTED, "anneal: " + why);
         // tiled e4m3 spin buffers; convert in, step, convert out
         uint8_t* t0 = nullptr;
         uint8_t* t1 = nullptr;
@@ -771,10 +788,20 @@ pbit_status pbit_fields_dense(pbit_graph g, const int8_t* spins, int32_t trials,
     pbit_status st = check_device(g);
     if (st != PBIT_OK) return st;
     std::string why;
-    if (!dense_shape_ok(*g, trials, &why)) return fail(PBIT_E_UNSUPPORTED, "fields_dense: " + why);
+    if (!any_dense_ok(*g, trials, &why)) return fail(PBIT_E_UNSUPPORTED, "fields_dense: " + why);
     cudaStream_t s = (cudaStream_t)stream;
     CallBuffers cb;
     cb.s = s;
+    if (dense4_shape_ok(*g, trials)) {
+        uint8_t* b0 = nullptr;
+        if ((st = cb.alloc(&b0, dense4_spin_bytes(*g, trials))) != PBIT_OK) return st;
+        StepArgs a{};
+        a.T = trials;
+        const cudaError_t de = launch_dense4(*g, a, spins, nullptr, fields, b0, 0, 0, s);
+        if (de == cudaSuccess) return PBIT_OK;
+        if (de != cudaErrorNotSupported) return cuda_fail(de, "fields_dense fp4");
+    }
+    if (!g->dense.J_e4m3) return fail(PBIT_E_UNSUPPORTED, "fields_dense: no e4m3 operand");
     uint8_t* t0 = nullptr;
     if ((st = cb.alloc(&t0, dense_spin_bytes(*g, trials))) != PBIT_OK) return st;
     PBIT_CUDA_TRY(launch_to_tiled(*g, spins, trials, t0, s));

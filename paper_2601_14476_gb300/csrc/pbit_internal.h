@@ -35,6 +35,14 @@ struct DenseOperand {
     size_t bytes = 0;
 };
 
+// The same J as packed e2m1 (FP4) for the cluster-resident dense kernel (pbit_dense4.cu): built
+// when n <= 2048 and every |J_ij| is 0, 1, 2, 3, 4 or 6 (exact in e2m1).
+struct Dense4Operand {
+    int32_t C = 0;             // row blocks of 128 = CTAs per cluster; K = 128 C
+    uint8_t* J4 = nullptr;     // device, C blocks of 64 K bytes
+    size_t bytes = 0;
+};
+
 // Tile dependencies of the multi-step sparse kernel for one item count per
 // node (groups = T / G): tile t may run step j once every tile in
 // idx[ptr[t] .. ptr[t+1]) has finished step j - 1; an empty list means "wait
@@ -75,6 +83,7 @@ struct Graph {
     int32_t max_wabs = 0;
     bool tab_ok = false;          // prefix sums fit int32
     DenseOperand dense;
+    Dense4Operand dense4;
     FlowDeps flow;                // built on first use, for the last groups value asked for
     int* err = nullptr;           // device word: nonzero after a bounded wait gave up
     size_t device_bytes = 0;
@@ -191,6 +200,15 @@ cudaError_t launch_dense_cut_energy(const Graph& g, const int8_t* spins, int32_t
                                     uint8_t* tiled_scratch, cudaStream_t st);
 cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t* buf0, uint8_t* buf1, int32_t b,
                                     int32_t e, unsigned* done, int* err, cudaStream_t st);
+// cluster-resident FP4 dense path (pbit_dense4.cu)
+pbit_status build_dense4_operand(Graph& g);
+bool dense4_shape_ok(const Graph& g, int32_t T);
+size_t dense4_spin_bytes(const Graph& g, int32_t T);
+// Steps [b, e) from s_in to s_out in one launch (in place allowed), or, with fields_out, the fields of
+// s_in only.  b0_scratch: dense4_spin_bytes(g, T) bytes.  cudaErrorNotSupported: not launched.
+cudaError_t launch_dense4(const Graph& g, const StepArgs& sa, const int8_t* s_in, int8_t* s_out, int32_t* fields_out,
+                          uint8_t* b0_scratch, int32_t b, int32_t e, cudaStream_t st);
+int dense4_max_active_clusters(const Graph& g, int32_t T);
 cudaError_t launch_bounded_wait_selftest(const unsigned* flag, long long budget_ns, int* err, cudaStream_t s);
 // resident single-CTA anneal: all steps in one launch, spins in shared memory
 bool resident_fits(const Graph& g, int32_t T);
