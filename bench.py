@@ -477,15 +477,18 @@ def run_single(args, w, variant, kernel, dense, steps, warmup, e2e_reps, dist, w
     pk = peaks()
     if chosen == pbit.KERNEL_DENSE:
         # 2 n^2 T flops per step (algorithmic, unpadded); the anneal is one kernel timed alone, so the
-        # peak is the burst one: e4m3 tensor peak = 2 x the measured bf16 burst peak (nominal ratio)
+        # peak is the burst one, scaled from the measured bf16 burst peak by the nominal dense ratio of
+        # the contraction's own type: packed e2m1 (FP4) 6x for the cluster-resident kernel, e4m3 2x
+        fp4 = (G.info()["has_dense_fp4"] == 1 and T % 16 == 0 and not os.environ.get("PBIT_DENSE_E4M3"))
         flops = 2.0 * g.n * g.n * T * S
         achieved = flops / (anneal_ms * 1e-3) / 1e12
-        peak = 2.0 * pk["bf16_tflops"]
+        ratio, kname = (6.0, "dense4_cluster_kernel") if fp4 else (2.0, "dense_persistent_kernel")
+        peak = ratio * pk["bf16_tflops"]
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic_for("dense_persistent_kernel"),
-                    "kernel": "dense_persistent_kernel",
-                    "peak_source": f"{pk['source']} bf16 burst x2 (e4m3 nominal ratio)",
-                    "per_launch": "2*n^2*T*S flops over one persistent launch (includes the two layout kernels)"}
+                    "frac": achieved / peak, "traffic": traffic_for(kname),
+                    "kernel": kname,
+                    "peak_source": f"{pk['source']} bf16 burst x{ratio:g} ({'e2m1' if fp4 else 'e4m3'} nominal ratio)",
+                    "per_launch": "2*n^2*T*S flops over one launch (includes the spin layout kernel)"}
     else:
         kname = sparse_tile_kernel(g, T, anneal_launches, S) if chosen == pbit.KERNEL_SPARSE else "resident_kernel"
         if variant:

@@ -67,7 +67,9 @@ int64_t pbit_launch_count(void);
 
 typedef struct pbit_graph_s* pbit_graph;
 
-#define PBIT_GRAPH_DENSE 1u     /* also build the dense tensor-core operand of J (|w| <= 16, n <= 8192) */
+#define PBIT_GRAPH_DENSE 1u     /* also build the dense tensor-core operands of J: e4m3 (|w| <= 16,
+                                   n <= 8192) and, where exact, packed e2m1 (n <= 2048, |w| in
+                                   {0,1,2,3,4,6}) for the cluster-resident kernel */
 
 /*
  * Create a MAX-CUT instance on the current CUDA device.
@@ -99,6 +101,8 @@ typedef struct {
     double mean_s;         /* mean_i sqrt((n-1) Var(J_i,:)), the schedule's normaliser */
     int64_t total_weight;  /* W = sum of w over edges (cut = (W - H)/2 when h = 0) */
     size_t device_bytes;   /* HBM held by the graph */
+    int32_t has_dense_fp4; /* 1 if the packed e2m1 operand of the cluster-resident dense kernel was built
+                              (PBIT_GRAPH_DENSE, n <= 2048, every |w| in {0,1,2,3,4,6}) */
 } pbit_graph_info_t;
 
 pbit_status pbit_graph_info(pbit_graph g, pbit_graph_info_t* info);

@@ -428,6 +428,7 @@ pbit_status pbit_graph_info(pbit_graph g, pbit_graph_info_t* info) {
     info->max_degree = g->max_degree;
     info->unit_weights = g->unit_weights ? 1 : 0;
     info->has_dense = g->dense.J_e4m3 ? 1 : 0;
+    info->has_dense_fp4 = g->dense4.J4 ? 1 : 0;
     info->device = g->device;
     info->mean_s = g->mean_s;
     info->total_weight = g->total_weight;

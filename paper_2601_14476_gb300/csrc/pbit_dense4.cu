@@ -13,19 +13,22 @@
 //
 // Work decomposition (one launch for the whole step range):
 //   cluster = C CTAs (C = ceil(n / 128) <= 16), one cluster per group of N
-//   trials (N = 32 or 64; grid = (C, groups)).  CTA r of a cluster holds
-//   rows 128r..128r+127 of J over all K = 128C columns in shared memory for
-//   the whole anneal (64K bytes: 128 KB at n = 2048) and two buffers of the
-//   group's spins in the MMA's B layout (K x N nibbles each).  Per step:
+//   trials (N = 32 or 48; grid = (C, groups)); GB300 keeps 7 clusters of 16
+//   CTAs resident, so 256 trials run as 6 groups of 48 in one wave.  CTA r of
+//   a cluster holds rows 128r..128r+127 of J over all K = 128C columns in
+//   shared memory for the whole anneal (64K bytes: 128 KB at n = 2048) and two
+//   buffers of the group's spins in the MMA's B layout (K x N nibbles each).
+//   Per step:
 //     1. the control thread waits until all C slices of the step's spins
 //        have arrived in the current buffer, issues K/64 MMAs
 //        (M = 128, N, K = 64) into TMEM and commits them to an mbarrier;
-//     2. the epilogue warps read the 128 x N fields from TMEM (warp w: lanes
-//        32(w%4).., 16 trial columns 16(w/4)..), take the p-bit decisions
-//        (Eq. pbits_variability, timing draw, Philox words drawn while the
-//        MMAs ran), pack the new spins of their 128 rows with warp ballots
-//        into this CTA's slice of the other buffer (64N bytes), and
-//     3. one thread copies that slice into the same place in the other C-1
+//     2. the epilogue warps (N/4 of them: warp w reads TMEM lanes 32(w%4)..
+//        and the 16 trial columns 16(w/4)..) take the p-bit decisions
+//        (Eq. pbits_variability, timing draw; the Philox words and I0 were
+//        drawn during the previous step's copies and MMAs), pack the new
+//        spins of their 32 rows with warp ballots into this CTA's slice of
+//        the other buffer (64N bytes), and
+//     3. C-1 lanes copy that slice into the same place in the other C-1
 //        CTAs' buffers with cp.async.bulk shared::cta -> shared::cluster,
 //        each copy completing on the receiver's mbarrier (bytes counted).
 //   A CTA's next step therefore waits only for the C-1 copies of its own
@@ -33,7 +36,10 @@
 //   The spins of a step are written to the buffer the step does not read,
 //   and a peer can only write a buffer again after this CTA's MMAs on it
 //   have completed (its copy depends on this CTA's next slice), so two
-//   buffers suffice.
+//   buffers suffice.  Measured step anatomy (K_2000, 48 trials per cluster,
+//   cycles of one CTA): 32 MMAs 2.8K (about 87 cycles each whatever N is),
+//   TMEM read 0.3K, decisions 2.9K, ballot packing and the epilogue barrier
+//   1.1K, slice copies 3.2K, about 10.6K in all.
 //
 // Layouts (no-swizzle K-major core matrices of 8 rows x 16 bytes = 8 x 32
 // nodes; leading byte offset = distance of K-adjacent core matrices, stride
@@ -52,6 +58,8 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "pbit_device.cuh"
@@ -185,6 +193,14 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// The p-bit input x of pbit_input for a field already held as an exact float (|D| < 2^24, so the
+// value equals pbit_input's for the same integer field).
+__device__ __forceinline__ float pbit_input_f(int mode, float I0, float lam, float del, float d) {
+    if (mode == 1) return __fmul_rn(__fmul_rn(lam, I0), __fadd_rn(d, del));
+    if (mode == 2) return __fmul_rn(lam, __fmaf_rn(I0, d, del));
+    return __fmul_rn(I0, __fmaf_rn(lam, d, del));
+}
+
 // Bit m of the low byte of x moved to bit 4m (m = 0..7).
 __device__ __forceinline__ uint32_t spread8(uint32_t x) {
     x &= 0xFFu;
@@ -221,27 +237,35 @@ struct D4Args {
     int* err;
 };
 
+// Shared memory: J rows (64K), two buffers of the FP4 spin operand (K N / 2 each), per-row
+// parameters, five mbarriers and the TMEM address.
 size_t d4_smem_bytes(int C, int N) {
     const size_t K = (size_t)kR * C;
-    return 1024 + 64 * K + K * (size_t)N + (size_t)kR * 16 + 64;
+    return 128 + 64 * K + K * (size_t)N + (size_t)kR * 16 + 8 * 5 + 16;
 }
 
-// Warps 0 .. E-1 (E = N/4) are the epilogue; warp E is the control warp.
+// Warps 0 .. E-1 (E = N/4: four lane quarters x N/16 groups of 16 trials) are the epilogue; warp E
+// is the control warp.
 template <int N>
 __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4Args a) {
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int C = a.C;
     const uint32_t K = (uint32_t)kR * C;
     const uint32_t bytesA = 64u * K, bytesB = K * (uint32_t)N / 2u, slice = 64u * (uint32_t)N;
     uint8_t* sA = smem;
-    uint8_t* const sB0 = sA + bytesA;  // buffer b at sB0 + b * bytesB
+    uint8_t* const sB0 = sA + bytesA;  // operand buffer b at sB0 + b * bytesB
     float* s_lam = (float*)(sB0 + 2 * (size_t)bytesB);
     float* s_del = s_lam + kR;
     uint32_t* s_thr = (uint32_t*)(s_del + kR);
     int32_t* s_h = (int32_t*)(s_thr + kR);
-    uint64_t* bars = (uint64_t*)(s_h + kR);  // 0, 1: full (B buffers), 2: MMA done, 3: J loaded
-    uint32_t* tmem_slot = (uint32_t*)(bars + 4);
+    // mbarriers: full[b] = every slice of operand buffer b is in (steps >= 1), then MMA done, J loaded,
+    // start spins loaded
+    uint64_t* full = (uint64_t*)(s_h + kR);
+    uint64_t* bar_mma = full + 2;
+    uint64_t* bar_j = bar_mma + 1;
+    uint64_t* bar_b0 = bar_mma + 2;
+    uint32_t* tmem_slot = (uint32_t*)(bar_mma + 3);
     __shared__ int s_abort;
 
     constexpr int E = N / 4;
@@ -259,7 +283,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (control && lane == 0) {
-        for (int k = 0; k < 4; ++k) mbar_init(&bars[k], 1);
+        for (int k = 0; k < 5; ++k) mbar_init(&full[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -288,21 +312,21 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
 
     if (control && lane == 0) {
         // J rows of this CTA (stationary) and the group's start spins
-        mbar_arrive_expect_tx(&bars[3], bytesA);
+        mbar_arrive_expect_tx(bar_j, bytesA);
         const uint8_t* gA = a.J4 + (size_t)rank * bytesA;
         for (uint32_t off = 0; off < bytesA; off += 65536u)
-            bulk_g2s(sA + off, gA + off, min(65536u, bytesA - off), &bars[3]);
-        mbar_arrive_expect_tx(&bars[0], bytesB);
+            bulk_g2s(sA + off, gA + off, min(65536u, bytesA - off), bar_j);
+        mbar_arrive_expect_tx(bar_b0, bytesB);
         const uint8_t* gB = a.B0 + (size_t)g * bytesB;
         for (uint32_t off = 0; off < bytesB; off += 65536u)
-            bulk_g2s(sB0 + off, gB + off, min(65536u, bytesB - off), &bars[0]);
-        if (!mbar_wait_bounded(&bars[3], 0)) {
+            bulk_g2s(sB0 + off, gB + off, min(65536u, bytesB - off), bar_b0);
+        if (!mbar_wait_bounded(bar_j, 0)) {
             atomicExch(a.err, 11);
             s_abort = 1;
         }
     }
 
-    // epilogue geometry: row rr of this CTA, trial columns c0 .. c0 + 15 of the group
+    // epilogue geometry: row rr of this CTA (one k core of 32 rows per warp), trials c0 .. c0 + 15
     const int quarter = warp & 3;
     const int rr = quarter * 32 + lane;
     const int i = (int)rank * kR + rr;
@@ -310,7 +334,8 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
     const int t0 = g * N + c0;           // first global trial of this thread
     uint32_t neg = 0;                    // bit j: trial t0 + j is -1 (the current state)
     uint4 rw[8];                         // Philox words of the step about to be decided
-    float lam = 1.0f, del = 0.0f;
+    float I0 = 0.0f;                     // I0 of the step about to be decided
+    float lam = 1.0f, del = 0.0f, hf = 0.0f;
     uint32_t thr = 1u << 24;
     int hi = 0;
     if (!control) {
@@ -318,6 +343,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         del = s_del[rr];
         thr = s_thr[rr];
         hi = s_h[rr];
+        hf = (float)hi;
         if (i < a.n && !fields_only) {
             for (int j = 0; j < 16; ++j) {
                 const int t = t0 + j;
@@ -325,6 +351,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
             }
         }
         if (L > 0) {
+            I0 = a.i0_table[a.step_begin];
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2)
                 rw[j2] = philox((uint32_t)i, (uint32_t)a.step_begin, (uint32_t)(t0 + 2 * j2) >> 1, a.instance,
@@ -342,7 +369,10 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
             // only lane 0 issues; the control warp leaves the loop as a whole once a wait gave up
             uint32_t ok = 1;
             if (lane == 0) {
-                ok = (s_abort == 0 && mbar_wait_bounded(&bars[buf], (uint32_t)((ls >> 1) & 1))) ? 1u : 0u;
+                ok = s_abort == 0 ? 1u : 0u;
+                // step 0 reads the start spins; step ls >= 1 the C slices of buffer ls & 1
+                if (ok) ok = (ls == 0 ? mbar_wait_bounded(bar_b0, 0)
+                                      : mbar_wait_bounded(&full[buf], (uint32_t)(((ls - 1) >> 1) & 1))) ? 1u : 0u;
                 if (ok) {
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB0 + (size_t)buf * bytesB);
@@ -350,7 +380,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
                         mma_mxf4(tmem, smem_desc(a0 + kk * 2 * lboA, lboA, 128),
                                  smem_desc(b0 + kk * 2 * lboB, lboB, 128), idesc, tmem + kSfaCol, tmem + kSfbCol,
                                  kk > 0 ? 1u : 0u);
-                    mma_commit(&bars[2]);
+                    mma_commit(bar_mma);
                 } else if (s_abort == 0) {
                     atomicExch(a.err, 12);
                 }
@@ -360,7 +390,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         }
         // ---- epilogue: wait (bounded) for this step's MMAs; the outcome is made uniform per warp
         uint32_t okw = 1;
-        if (lane == 0) okw = mbar_wait_bounded(&bars[2], (uint32_t)(ls & 1)) ? 1u : 0u;
+        if (lane == 0) okw = mbar_wait_bounded(bar_mma, (uint32_t)(ls & 1)) ? 1u : 0u;
         okw = __shfl_sync(0xFFFFFFFFu, okw, 0);
         if (!okw) {
             good = false;
@@ -385,12 +415,12 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         }
         const int step = a.step_begin + ls;
         if (okw) {
-            const float I0 = a.i0_table[step];
             uint32_t nneg = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int D = hi + __float2int_rn(__uint_as_float(v[j]));
-                const uint32_t kthr = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, D));
+                // D = h + (J s), both exact integers below 2^24: one float addition, no conversions
+                const float D = __fadd_rn(hf, __uint_as_float(v[j]));
+                const uint32_t kthr = pbit_kthr_of_x(pbit_input_f(a.offset_mode, I0, lam, del, D));
                 const uint4 w = rw[j >> 1];
                 const int old = (neg >> j) & 1u ? -1 : 1;
                 const int s = (j & 1) ? pbit_next(w.z, w.w, kthr, thr, old) : pbit_next(w.x, w.y, kthr, thr, old);
@@ -399,7 +429,8 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
             neg = nneg;
         }
         if (ls + 1 == L) break;
-        uint8_t* dstB = sB0 + (size_t)(buf ^ 1) * bytesB;
+        const uint32_t nb = (uint32_t)(buf ^ 1);
+        uint8_t* dstB = sB0 + (size_t)nb * bytesB;
         if (okw) {
             // this warp's 32 rows are one k core (kc = 4 rank + quarter); lane j < 16 writes trial c0 + j
             uint32_t mine = 0;
@@ -430,18 +461,20 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
             good = false;
             break;
         }
-        if (tid == 0) {
-            // the C-1 peers' copies complete on this barrier; this thread's arrival is the local one
-            uint64_t* full = &bars[buf ^ 1];
-            mbar_arrive_expect_tx(full, slice * (uint32_t)(C - 1));
+        if (warp == 0) {
+            // lane 0 makes the local arrival (the C-1 peers' copies complete on the same barrier);
+            // lanes 1 .. C-1 each copy this CTA's slice into one peer
+            uint64_t* nfull = &full[nb];
             const uint8_t* src = dstB + rank * slice;
-            const uint32_t dst_local = smem_u32(src), bar_local = smem_u32(full);
-            for (uint32_t p = 1; p < (uint32_t)C; ++p) {
-                const uint32_t peer = (rank + p) % (uint32_t)C;
-                bulk_s2peer(map_rank(dst_local, peer), src, slice, map_rank(bar_local, peer));
+            if (lane == 0) {
+                mbar_arrive_expect_tx(nfull, slice * (uint32_t)(C - 1));
+            } else if (lane < C) {
+                const uint32_t peer = (rank + (uint32_t)lane) % (uint32_t)C;
+                bulk_s2peer(map_rank(smem_u32(src), peer), src, slice, map_rank(smem_u32(nfull), peer));
             }
         }
-        // Philox words of the next step, drawn while the copies and the next MMAs run
+        // I0 and the Philox words of the next step, drawn while the copies and the next MMAs run
+        I0 = a.i0_table[step + 1];
 #pragma unroll
         for (int j2 = 0; j2 < 8; ++j2)
             rw[j2] = philox((uint32_t)i, (uint32_t)(step + 1), (uint32_t)(t0 + 2 * j2) >> 1, a.instance, a.seed_lo,
@@ -549,17 +582,23 @@ pbit_status build_dense4_operand(Graph& g) {
     return PBIT_OK;
 }
 
-// Trials per cluster: the larger of 64 and 32 whose buffers fit one CTA's shared memory, no larger
-// than the trial count needs.
+template <int N>
+static int max_clusters_d4(int C);
+
+// Trials per cluster N (32 or 48, the buffers must fit one CTA's shared memory): the smallest N
+// whose groups all run at once (ceil(T / N) clusters co-resident), else the largest N that fits.
 static int dense4_group(const Graph& g, int32_t T) {
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    for (int N : {64, 32}) {
-        if (N > 32 && T <= N / 2) continue;
-        if (d4_smem_bytes(g.dense4.C, N) <= (size_t)smem_max) return N;
+    int best = 0;
+    for (int N : {32, 48}) {
+        if (d4_smem_bytes(g.dense4.C, N) + 256 > (size_t)smem_max) continue;  // + static shared memory
+        best = N;
+        const int m = N == 32 ? max_clusters_d4<32>(g.dense4.C) : max_clusters_d4<48>(g.dense4.C);
+        if (m >= (T + N - 1) / N) return N;
     }
-    return 0;
+    return best;
 }
 
 size_t dense4_spin_bytes(const Graph& g, int32_t T) {
@@ -609,12 +648,22 @@ static cudaError_t launch_d4(const D4Args& a, cudaStream_t st) {
 
 template <int N>
 static int max_clusters_d4(int C) {
+    // cached per (device, C): an occupancy query per anneal would cost more than a short anneal
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({dev, C});
+    if (it != cache.end()) return it->second;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
-    if (d4_config<N>(C, cfg, attr) != cudaSuccess) return 0;
-    cfg.gridDim = dim3((unsigned)C, 1, 1);
     int m = 0;
-    if (cudaOccupancyMaxActiveClusters(&m, dense4_cluster_kernel<N>, &cfg) != cudaSuccess) return 0;
+    if (d4_config<N>(C, cfg, attr) == cudaSuccess) {
+        cfg.gridDim = dim3((unsigned)C, 1, 1);
+        if (cudaOccupancyMaxActiveClusters(&m, dense4_cluster_kernel<N>, &cfg) != cudaSuccess) m = 0;
+    }
+    cache[{dev, C}] = m;
     return m;
 }
 
@@ -648,13 +697,13 @@ cudaError_t launch_dense4(const Graph& g, const StepArgs& sa, const int8_t* s_in
     a.instance = sa.instance;
     a.offset_mode = sa.offset_mode;
     a.err = g.err;
-    return N == 64 ? launch_d4<64>(a, st) : launch_d4<32>(a, st);
+    return N == 48 ? launch_d4<48>(a, st) : launch_d4<32>(a, st);
 }
 
 int dense4_max_active_clusters(const Graph& g, int32_t T) {
     const int N = dense4_group(g, T);
     if (N == 0 || !g.dense4.J4) return 0;
-    return N == 64 ? max_clusters_d4<64>(g.dense4.C) : max_clusters_d4<32>(g.dense4.C);
+    return N == 48 ? max_clusters_d4<48>(g.dense4.C) : max_clusters_d4<32>(g.dense4.C);
 }
 
 }  // namespace pbit

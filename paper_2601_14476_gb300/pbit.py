@@ -45,7 +45,7 @@ class PbitError(RuntimeError):
 class pbit_graph_info_t(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_edges", C.c_int64), ("max_degree", C.c_int32), ("unit_weights", C.c_int32),
                 ("has_dense", C.c_int32), ("device", C.c_int32), ("mean_s", C.c_double),
-                ("total_weight", C.c_int64), ("device_bytes", C.c_size_t)]
+                ("total_weight", C.c_int64), ("device_bytes", C.c_size_t), ("has_dense_fp4", C.c_int32)]
 
 
 class pbit_anneal_params(C.Structure):

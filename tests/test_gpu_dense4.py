@@ -124,7 +124,7 @@ _CHILD = (
     "import numpy as np, torch\n"
     "from paper_2601_14476_gb300 import inputs, pbit\n"
     "outs = []\n"
-    "cases = ((inputs.complete_pm1(2000, 1), 256, 120), (inputs.complete_pm1(300, 2), 48, 90),\n"
+    "cases = ((inputs.complete_pm1(2000, 1), 256, 120), (inputs.complete_pm1(300, 2), 96, 90),\n"
     "         (inputs.complete_pm1(128, 3), 32, 77), (inputs.complete_pm1(900, 4), 64, 60))\n"
     "for g, T, S in cases:\n"
     "    G = pbit.Graph.from_inputs(g, dense=True)\n"
