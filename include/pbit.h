@@ -23,8 +23,8 @@
  *    stream.  Work is enqueued on it in order; entry points that return
  *    results in host memory synchronise that stream before returning.
  *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key =
- *    (seed low word, seed high word) and counter = (node, step, trial/2,
- *    instance); the even trial of a pair uses output words (0,1), the odd one
+ *    (seed low word, seed high word) and counter = (node, step, instance,
+ *    trial/2); the even trial of a pair uses output words (0,1), the odd one
  *    (2,3), as (r, u): r = (2*(w0>>8)+1-2^24)/2^24, u = (w1>>8)/2^24.  The
  *    initial state (step counter 0xFFFFFFFF) is +1 iff r < 0.  Results are
  *    therefore a pure function of (graph, parameters, seed, instance) and do

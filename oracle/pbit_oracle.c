@@ -37,8 +37,8 @@
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), written here from that paper's
- * definition.  key = (seed_lo, seed_hi); counter = (node, step, trial/2,
- * instance); trial parity selects output words (0,1) or (2,3) as (r, u).
+ * definition.  key = (seed_lo, seed_hi); counter = (node, step, instance,
+ * trial/2); trial parity selects output words (0,1) or (2,3) as (r, u).
  * The initial state uses step = 0xFFFFFFFF and sets +1 iff r < 0.
  *
  * Pins (tests/test_oracle_pins.py): brute-force MAX-CUT for n <= 20, the
@@ -94,7 +94,7 @@ typedef struct {
 } orc_draw;
 
 static orc_draw orc_draw_for(uint64_t seed, uint32_t instance, int32_t node, uint32_t step, int32_t trial) {
-    uint32_t ctr[4] = {(uint32_t)node, step, (uint32_t)trial >> 1, instance};
+    uint32_t ctr[4] = {(uint32_t)node, step, instance, (uint32_t)trial >> 1};
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
@@ -408,14 +408,14 @@ int orc_anneal(int32_t n, const int32_t* row_ptr, const int32_t* col, const int8
 /*   EQUATION x = lambda (I + delta)  (each reduces to the pSA form when    */
 /*   I = I0 D).  Random words: (r, u) as for pSA at counter step q; the     */
 /*   SpSA stall draw is word (trial mod 4) of Philox at counter (node, q,   */
-/*   trial / 4, instance ^ 0x80000000), stall iff its top 24 bits / 2^24 < p.*/
+/*   instance ^ 0x80000000, trial / 4), stall iff top 24 bits / 2^24 < p.   */
 /* ------------------------------------------------------------------ */
 #define ORC_ALG_PSA 0
 #define ORC_ALG_SPSA 1
 #define ORC_ALG_TAPSA 2
 
 static double orc_stall_draw(uint64_t seed, uint32_t instance, int32_t node, uint32_t step, int32_t trial) {
-    uint32_t ctr[4] = {(uint32_t)node, step, (uint32_t)trial >> 2, instance ^ 0x80000000u};
+    uint32_t ctr[4] = {(uint32_t)node, step, instance ^ 0x80000000u, (uint32_t)trial >> 2};
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);

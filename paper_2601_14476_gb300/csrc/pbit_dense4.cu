@@ -352,10 +352,10 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         }
         if (L > 0) {
             I0 = a.i0_table[a.step_begin];
+            const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step_begin, a.instance, a.seed_lo, a.seed_hi);
 #pragma unroll
             for (int j2 = 0; j2 < 8; ++j2)
-                rw[j2] = philox((uint32_t)i, (uint32_t)a.step_begin, (uint32_t)(t0 + 2 * j2) >> 1, a.instance,
-                                a.seed_lo, a.seed_hi);
+                rw[j2] = philox_tail(ph, (uint32_t)(t0 + 2 * j2) >> 1, a.seed_lo, a.seed_hi);
         }
     }
     const uint32_t idesc = idesc_mxf4((uint32_t)N);
@@ -475,10 +475,9 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         }
         // I0 and the Philox words of the next step, drawn while the copies and the next MMAs run
         I0 = a.i0_table[step + 1];
+        const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)(step + 1), a.instance, a.seed_lo, a.seed_hi);
 #pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2)
-            rw[j2] = philox((uint32_t)i, (uint32_t)(step + 1), (uint32_t)(t0 + 2 * j2) >> 1, a.instance, a.seed_lo,
-                            a.seed_hi);
+        for (int j2 = 0; j2 < 8; ++j2) rw[j2] = philox_tail(ph, (uint32_t)(t0 + 2 * j2) >> 1, a.seed_lo, a.seed_hi);
     }
     // final state of this thread's row and trials (left untouched when a wait gave up: the result of
     // that call is undefined and PBIT_E_TIMEOUT reports it)

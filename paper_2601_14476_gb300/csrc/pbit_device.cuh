@@ -29,11 +29,16 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
-// Two Philox4x32-10 blocks whose counters differ only in the third word,
+// Two Philox4x32-10 blocks whose counters differ only in the last word,
 // evaluated side by side (independent instruction streams for the scheduler).
-__device__ __forceinline__ void philox_pair(uint32_t c0, uint32_t c1, uint32_t c2a, uint32_t c2b, uint32_t c3,
+// The counters of this library put the per-trial word last: (node, step,
+// instance, trial pair).  The first round's two products and the second
+// round's first product then do not depend on the trial, so a thread that
+// draws for many trials of one node shares them (16 rather than 19 wide
+// multiplies per block once inlined).
+__device__ __forceinline__ void philox_pair(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3a, uint32_t c3b,
                                             uint32_t k0, uint32_t k1, uint4& ra, uint4& rb) {
-    uint32_t a0 = c0, a1 = c1, a2 = c2a, a3 = c3, b0 = c0, b1 = c1, b2 = c2b, b3 = c3;
+    uint32_t a0 = c0, a1 = c1, a2 = c2, a3 = c3a, b0 = c0, b1 = c1, b2 = c2, b3 = c3b;
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
         if (round) {
@@ -55,6 +60,69 @@ __device__ __forceinline__ void philox_pair(uint32_t c0, uint32_t c1, uint32_t c
     }
     ra = make_uint4(a0, a1, a2, a3);
     rb = make_uint4(b0, b1, b2, b3);
+}
+
+// Philox4x32-10 split at the last counter word.  For counters (c0, c1, c2, c3)
+// the first round's two products, and the second round's product of the
+// first word, do not depend on c3; PhiloxHead keeps what the rest of the
+// rounds need of them, so a thread drawing for many values of c3 (the trial
+// pairs of one node) computes them once and each block then costs 16 wide
+// multiplies.  philox_tail(philox_head(c0, c1, c2, k), c3, k) equals
+// philox(c0, c1, c2, c3, k).
+struct PhiloxHead {
+    uint32_t y1;   // round-1 output word 1
+    uint32_t h2;   // round-1 output word 2 without the c3 term
+    uint32_t z3;   // round-2 output word 3
+    uint32_t hp1;  // high half of the round-3 product of word 2
+    uint32_t w1;   // round-3 output word 1
+};
+
+__device__ __forceinline__ PhiloxHead philox_head(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t k0, uint32_t k1) {
+    PhiloxHead h;
+    // round 1 (keys k0, k1)
+    const uint64_t a0 = (uint64_t)0xD2511F53u * c0, a1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t y0 = (uint32_t)(a1 >> 32) ^ c1 ^ k0;
+    h.y1 = (uint32_t)a1;
+    h.h2 = (uint32_t)(a0 >> 32) ^ k1;
+    const uint32_t y3 = (uint32_t)a0;
+    // round 2: the product of word 0 (keys + 1 increment)
+    const uint64_t b0 = (uint64_t)0xD2511F53u * y0;
+    const uint32_t z2 = (uint32_t)(b0 >> 32) ^ y3 ^ (k1 + 0xBB67AE85u);
+    h.z3 = (uint32_t)b0;
+    // round 3: the product of word 2
+    const uint64_t c1p = (uint64_t)0xCD9E8D57u * z2;
+    h.hp1 = (uint32_t)(c1p >> 32);
+    h.w1 = (uint32_t)c1p;
+    return h;
+}
+
+__device__ __forceinline__ uint4 philox_tail(const PhiloxHead& h, uint32_t c3, uint32_t k0, uint32_t k1) {
+    // round 1, word 2; round 2, word 2 product
+    const uint32_t y2 = h.h2 ^ c3;
+    const uint64_t b1 = (uint64_t)0xCD9E8D57u * y2;
+    const uint32_t z0 = (uint32_t)(b1 >> 32) ^ h.y1 ^ (k0 + 0x9E3779B9u);
+    const uint32_t z1 = (uint32_t)b1;
+    // round 3, word 0 product (keys + 2 increments)
+    const uint64_t c0p = (uint64_t)0xD2511F53u * z0;
+    uint32_t x0 = h.hp1 ^ z1 ^ (k0 + 2u * 0x9E3779B9u);
+    uint32_t x1 = h.w1;
+    uint32_t x2 = (uint32_t)(c0p >> 32) ^ h.z3 ^ (k1 + 2u * 0xBB67AE85u);
+    uint32_t x3 = (uint32_t)c0p;
+    k0 += 2u * 0x9E3779B9u;
+    k1 += 2u * 0xBB67AE85u;
+#pragma unroll
+    for (int round = 3; round < 10; ++round) {
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0, n2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        x0 = n0;
+        x1 = (uint32_t)p1;
+        x2 = n2;
+        x3 = (uint32_t)p0;
+    }
+    return make_uint4(x0, x1, x2, x3);
 }
 
 // The p-bit input x for an exact integer field D (three placements of the

@@ -91,7 +91,7 @@ __device__ __forceinline__ void decide_group(const StepArgs& a, int i, int t0, c
 #pragma unroll
     for (int k = 0; k < Pack<G>::W; ++k) neww[k] = 0;
     if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
+        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
         const bool odd = t0 & 1;
         const uint32_t wr = odd ? r.z : r.x, wu = odd ? r.w : r.y;
         const uint32_t kthr = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[0]));
@@ -100,7 +100,7 @@ __device__ __forceinline__ void decide_group(const StepArgs& a, int i, int t0, c
     } else {
 #pragma unroll
         for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo,
+            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)(t0 + k) >> 1, a.seed_lo,
                                    a.seed_hi);
             const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k]));
             const uint32_t k1 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k + 1]));
@@ -235,17 +235,18 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
     uint32_t oldw[NW], neww[NW];
     load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
     if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
+        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
         const bool odd = t0 & 1;
         const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr_at(0), thr, sbyte(oldw[0], 0));
         neww[0] = (uint32_t)(uint8_t)(int8_t)s;
     } else {
         // sign tests and byte masks as in the warp-table tile
+        const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step, a.instance, a.seed_lo, a.seed_hi);
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             uint4 r[2];
-            philox_pair((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + 4 * w) >> 1, (uint32_t)(t0 + 4 * w + 2) >> 1,
-                        a.instance, a.seed_lo, a.seed_hi, r[0], r[1]);
+            r[0] = philox_tail(ph, (uint32_t)(t0 + 4 * w) >> 1, a.seed_lo, a.seed_hi);
+            r[1] = philox_tail(ph, (uint32_t)(t0 + 4 * w + 2) >> 1, a.seed_lo, a.seed_hi);
             uint32_t dr[4], du[4];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -315,11 +316,12 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     }
     uint32_t oldw[NW], neww[NW];
     load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
+    const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step, a.instance, a.seed_lo, a.seed_hi);
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         uint4 r[2];
-        philox_pair((uint32_t)i, (uint32_t)a.step, (uint32_t)(t0 + 4 * w) >> 1, (uint32_t)(t0 + 4 * w + 2) >> 1,
-                    a.instance, a.seed_lo, a.seed_hi, r[0], r[1]);
+        r[0] = philox_tail(ph, (uint32_t)(t0 + 4 * w) >> 1, a.seed_lo, a.seed_hi);
+        r[1] = philox_tail(ph, (uint32_t)(t0 + 4 * w + 2) >> 1, a.seed_lo, a.seed_hi);
         uint32_t dr[4], du[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -410,7 +412,7 @@ __device__ __forceinline__ void process_tile_variant(const StepArgs& a, int64_t 
         for (int k = 0; k < G; ++k) {
             const int t = t0 + k;
             if (k == 0 || (t & 3) == 0)
-                sw = philox((uint32_t)i, q, (uint32_t)t >> 2, a.instance ^ 0x80000000u, a.seed_lo, a.seed_hi);
+                sw = philox((uint32_t)i, q, a.instance ^ 0x80000000u, (uint32_t)t >> 2, a.seed_lo, a.seed_hi);
             const uint32_t word = (t & 3) == 0 ? sw.x : ((t & 3) == 1 ? sw.y : ((t & 3) == 2 ? sw.z : sw.w));
             const bool stall = (word >> 8) < a.stall_thr;
             I[k] = stall ? a.Iprev[base + k] : __fmul_rn(I0, (float)D[k]);
@@ -434,7 +436,7 @@ __device__ __forceinline__ void process_tile_variant(const StepArgs& a, int64_t 
 #pragma unroll
     for (int w = 0; w < Pack<G>::W; ++w) neww[w] = 0;
     if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, q, (uint32_t)t0 >> 1, a.instance, a.seed_lo, a.seed_hi);
+        const uint4 r = philox((uint32_t)i, q, a.instance, (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
         const bool odd = t0 & 1;
         const uint32_t kthr = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[0]));
         const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr, thr, sbyte(oldw[0], 0));
@@ -442,7 +444,7 @@ __device__ __forceinline__ void process_tile_variant(const StepArgs& a, int64_t 
     } else {
 #pragma unroll
         for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, q, (uint32_t)(t0 + k) >> 1, a.instance, a.seed_lo, a.seed_hi);
+            const uint4 r = philox((uint32_t)i, q, a.instance, (uint32_t)(t0 + k) >> 1, a.seed_lo, a.seed_hi);
             const uint32_t k0 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k]));
             const uint32_t k1 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k + 1]));
             const int s0 = pbit_next(r.x, r.y, k0, thr, sbyte(oldw[k >> 2], k & 3));

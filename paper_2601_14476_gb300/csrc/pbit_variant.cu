@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words
         float I[4];
         if (a.alg == 1) {
             // SpSA: stall draw of trial t + b = word b of Philox(node, q, t / 4, instance ^ 2^31)
-            const uint4 sw = philox((uint32_t)i, q, (uint32_t)t >> 2, a.instance ^ 0x80000000u, a.seed_lo, a.seed_hi);
+            const uint4 sw = philox((uint32_t)i, q, a.instance ^ 0x80000000u, (uint32_t)t >> 2, a.seed_lo, a.seed_hi);
             I[0] = (sw.x >> 8) < a.stall_thr ? prev[k].x : __fmul_rn(I0, (float)D[4 * k]);
             I[1] = (sw.y >> 8) < a.stall_thr ? prev[k].y : __fmul_rn(I0, (float)D[4 * k + 1]);
             I[2] = (sw.z >> 8) < a.stall_thr ? prev[k].z : __fmul_rn(I0, (float)D[4 * k + 2]);
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kVBlock, NW >= 4 ? 3 : 4) sparse_variant_words
         }
         // decisions (Eq. 6): candidate +1 iff r-word k-value < kthr, update iff u-word < thr
         uint4 r0, r1;
-        philox_pair((uint32_t)i, q, (uint32_t)t >> 1, (uint32_t)(t + 2) >> 1, a.instance, a.seed_lo, a.seed_hi, r0,
+        philox_pair((uint32_t)i, q, a.instance, (uint32_t)t >> 1, (uint32_t)(t + 2) >> 1, a.seed_lo, a.seed_hi, r0,
                     r1);
         uint32_t nk[4];
         if (table) {

@@ -53,10 +53,11 @@ def test_philox_matches_triton_interpreter():
 
 
 def test_philox_output_statistics():
-    """2^16 blocks at consecutive trial counters: every bit set half the time, the top byte of each
-    word uniform (chi-square, 255 dof) and the top nibbles of the r and u words of one trial independent
-    (chi-square, 255 dof), both within five standard deviations."""
-    words = np.array([oracle.philox4x32_10([node, 3, t, 0], [0x1234, 0x9876])
+    """2^16 blocks at consecutive trial counters (the last counter word, as the draws use them): every
+    bit set half the time, the top byte of each word uniform (chi-square, 255 dof) and the top nibbles
+    of the r and u words of one trial independent (chi-square, 255 dof), both within five standard
+    deviations."""
+    words = np.array([oracle.philox4x32_10([node, 3, 0, t], [0x1234, 0x9876])
                       for node in range(16) for t in range(4096)], dtype=np.uint32)
     flat = words.ravel()
     bits = ((flat[:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(axis=0)
@@ -398,7 +399,7 @@ def test_init_spins_rule_against_triton_philox():
     seed, instance = 0x1234_5678_9ABC, 5
     key = [seed & 0xFFFFFFFF, seed >> 32]
     pairs = [(i, t) for i in (0, 1, 7, 40) for t in range(6)]
-    cases = [([i, 0xFFFFFFFF, t >> 1, instance], key) for i, t in pairs]
+    cases = [([i, 0xFFFFFFFF, instance, t >> 1], key) for i, t in pairs]
     script = os.path.join(ROOT, "tests", "golden", "triton_philox.py")
     res = subprocess.run([sys.executable, script], input=json.dumps(cases), capture_output=True, text=True,
                          env=dict(os.environ, TRITON_INTERPRET="1"), timeout=600)
