@@ -293,8 +293,8 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     const int i = (int)(((unsigned long long)item * a.grp_m) >> a.grp_s);
     const int t0 = (int)(item - (uint32_t)i * groups) * G;
     const int lane = (int)(tid & 31u);
-    const int L = groups >= 32u ? 32 : (int)groups;
-    const int seg = lane & ~(L - 1), ell = lane & (L - 1);
+    const int L = groups >= 32u ? 32 : (int)groups;  // a power of two: T / G divides 32 or is a multiple
+    const int ell = lane & (L - 1);
     const float I0 = __ldg(a.i0_table + a.step);
     const int hi = a.h ? __ldg(a.h + i) : 0;
     const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
@@ -306,7 +306,18 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     uint32_t cnt2[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) cnt2[w] = 0;
-    for (int e = rb; e < re; ++e) {
+    // two neighbours per iteration: both loads in flight, one three-input add per word
+    int e = rb;
+    for (; e + 1 < re; e += 2) {
+        const int j0 = __ldg(a.col + e), j1 = __ldg(a.col + e + 1);
+        const uint32_t f0 = __ldg(a.J + e) < 0 ? 0x02020202u : 0u, f1 = __ldg(a.J + e + 1) < 0 ? 0x02020202u : 0u;
+        uint32_t v0[NW], v1[NW];
+        load_group<G>(a.in + (size_t)j0 * a.T + t0, v0);
+        load_group<G>(a.in + (size_t)j1 * a.T + t0, v1);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) cnt2[w] += ((v0[w] & 0x02020202u) ^ f0) + ((v1[w] & 0x02020202u) ^ f1);
+    }
+    if (e < re) {
         const int j = __ldg(a.col + e);
         const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
         uint32_t v[NW];
@@ -325,8 +336,9 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
         uint32_t dr[4], du[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, negk_lane, seg + (int)byte_of(cnt2[w], 2 * h));
-            const uint32_t q1 = __shfl_sync(0xFFFFFFFFu, negk_lane, seg + (int)byte_of(cnt2[w], 2 * h + 1));
+            // the shuffle width L keeps the source lane inside this node's segment
+            const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt2[w], 2 * h), L);
+            const uint32_t q1 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt2[w], 2 * h + 1), L);
             dr[2 * h] = (r[h].x >> 8) + q0;
             du[2 * h] = (r[h].y >> 8) - thr;
             dr[2 * h + 1] = (r[h].z >> 8) + q1;
