@@ -115,6 +115,19 @@ struct CallBuffers {
     }
 };
 
+TestFault test_fault(const char* kernel, long long default_cycles) {
+    TestFault f;
+    f.wait_cycles = default_cycles;
+    const char* w = std::getenv("PBIT_TEST_WITHHOLD");
+    if (!w || std::string(w) != kernel) return f;
+    f.withhold = 1;
+    if (const char* us = std::getenv("PBIT_TEST_WAIT_US")) {
+        const long long v = std::atoll(us);
+        if (v > 0 && v < 2000000) f.wait_cycles = v * 2000;  // about 2 GHz SM clock
+    }
+    return f;
+}
+
 // Either dense kernel can run T trials on this graph: the cluster-resident FP4 kernel or the e4m3 one.
 static bool any_dense_ok(const Graph& g, int32_t T, std::string* why) {
     return dense4_shape_ok(g, T) || dense_shape_ok(g, T, why);

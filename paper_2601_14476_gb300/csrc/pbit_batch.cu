@@ -53,6 +53,8 @@ struct ChunkArgs {
     unsigned* queue;             // item counter
     unsigned* tiles_done;        // [count] tiles finished in this chunk
     int* err;
+    long long wait_cycles;       // clock64 budget of each step wait (about a second; shorter in tests)
+    int withhold;                // test-only: instance 0's first tile of a chunk is never counted
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -103,7 +105,8 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_
     __shared__ int s_ok;
     const unsigned total = (unsigned)c.K * (unsigned)c.total_tiles;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(c.queue, 1u);
+        // once any wait has given up, every CTA stops claiming
+        if (threadIdx.x == 0) s_item = *(volatile int*)c.err != 0 ? total : atomicAdd(c.queue, 1u);
         __syncthreads();
         const unsigned idx = s_item;
         __syncthreads();  // s_item is read by everyone before thread 0 may overwrite it
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_
                 const unsigned need = (unsigned)k * (unsigned)d.tiles;
                 const long long start = clock64();
                 while (ld_acquire_u32(c.tiles_done + g) < need) {
-                    if (clock64() - start > (1ll << 31)) {
+                    if (clock64() - start > c.wait_cycles) {
                         atomicExch(c.err, 4);
                         ok = 0;
                         break;
@@ -135,6 +138,7 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_
             s_ok = ok;
         }
         __syncthreads();
+        if (!s_ok) break;  // uniform: s_ok was written before the barrier
         StepArgs a = d.a;
         a.step = d.cur + k;
         const int par = (d.parity + k) & 1;
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_
         dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
         __threadfence();  // this thread's spin stores, before the tile is counted
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(c.tiles_done + g, 1u);
+        if (threadIdx.x == 0 && !(c.withhold && g == 0 && k == 0 && tile_i == 0)) atomicAdd(c.tiles_done + g, 1u);
     }
 }
 
@@ -406,6 +410,11 @@ pbit_status ensure_graph(pbit_batch b, cudaStream_t user) {
     c.queue = b->d_ctl;
     c.tiles_done = b->d_ctl + 1;
     c.err = nullptr;
+    {
+        const TestFault tf = test_fault("batch", 1ll << 31);
+        c.wait_cycles = tf.wait_cycles;
+        c.withhold = tf.withhold;
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -729,6 +738,9 @@ void server_loop(pbit_server_s* S) {
         c.queue = S->d_ctl;
         c.tiles_done = S->d_ctl + 1;
         c.err = S->d_err;
+        const TestFault tf = test_fault("batch", 1ll << 31);
+        c.wait_cycles = tf.wait_cycles;
+        c.withhold = tf.withhold;
         bool variants = false;
         for (int32_t k = 0; k < count; ++k) variants = variants || is_variant(desc[(size_t)k].a);
         int sms = 0;
@@ -742,6 +754,17 @@ void server_loop(pbit_server_s* S) {
             admit(lk);
         }
         cudaError_t ce = cudaStreamSynchronize(S->stream);
+        // a bounded wait that gave up stopped the chunk: the resident requests fail with PBIT_E_TIMEOUT
+        int herr = 0;
+        if (ce == cudaSuccess) {
+            ce = cudaMemcpyAsync(&herr, S->d_err, sizeof(int), cudaMemcpyDeviceToHost, S->stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(S->stream);
+        }
+        const bool timed_out = ce == cudaSuccess && herr != 0;
+        if (timed_out) {
+            cudaMemsetAsync(S->d_err, 0, sizeof(int), S->stream);
+            cudaStreamSynchronize(S->stream);
+        }
         const auto t1 = Clock::now();
         // retire finished instances
         std::vector<Request*> finished;
@@ -751,12 +774,13 @@ void server_loop(pbit_server_s* S) {
             const int ran = std::min(S->chunk, std::max(0, d.end - d.cur));
             d.cur += ran;
             d.parity = (d.parity + ran) & 1;
-            if (d.cur >= d.end || ce != cudaSuccess) finished.push_back(r);
+            if (d.cur >= d.end || ce != cudaSuccess || timed_out) finished.push_back(r);
         }
         for (Request* r : finished) {
             r->cuts.assign((size_t)r->p.trials, 0);
-            pbit_status st = ce == cudaSuccess ? padded_cuts(r->g, r->desc, r->cuts.data(), S->stream)
-                                               : cuda_fail(ce, "server chunk");
+            pbit_status st = timed_out ? fail(PBIT_E_TIMEOUT, "server chunk: a bounded device-side wait gave up")
+                             : ce == cudaSuccess ? padded_cuts(r->g, r->desc, r->cuts.data(), S->stream)
+                                                 : cuda_fail(ce, "server chunk");
             for (void* p : r->allocs) cudaFreeAsync(p, S->stream);
             r->allocs.clear();
             std::lock_guard<std::mutex> lk(S->mu);

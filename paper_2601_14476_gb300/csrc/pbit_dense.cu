@@ -386,6 +386,8 @@ struct PersistArgs {
     int32_t step_begin, step_end;
     unsigned* done;   // [RB * TB], zero on entry
     int32_t tb_base;  // first trial block of this launch (launches cover consecutive groups)
+    long long wait_cycles;  // clock64 budget of each producer-flag wait (about a second; shorter in tests)
+    int32_t withhold;       // test-only: CTA (0, 0, tb_base) never publishes its progress
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                     bool ready = true;
                     for (int f = lane; f < nprod; f += 32) ready = ready && ld_acquire(prod0 + f) >= (unsigned)ls;
                     if (__all_sync(0xFFFFFFFFu, ready)) break;
-                    if (__shfl_sync(0xFFFFFFFFu, (int)(clock64() - start > (1ll << 31)), 0)) {
+                    if (__shfl_sync(0xFFFFFFFFu, (int)(clock64() - start > pa.wait_cycles), 0)) {
                         ok = false;
                         break;
                     }
@@ -650,7 +652,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
         // consumer acquires the flag and fences the async proxy before its bulk copy.
         if (!control) {
             asm volatile("bar.sync 1, %0;" ::"r"(kEpi) : "memory");
-            if (tid == 0) st_release(pa.done + ((size_t)tb * RB + rb) * a.KS + ks, (unsigned)(ls + 1));
+            if (tid == 0 && !(pa.withhold && ks == 0 && rb == 0 && tb == pa.tb_base))
+                st_release(pa.done + ((size_t)tb * RB + rb) * a.KS + ks, (unsigned)(ls + 1));
         }
     }
     tc_fence_before();
@@ -659,6 +662,11 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     }
+    // The last step's epilogue reads every peer's partials through distributed shared memory and
+    // no step follows whose cluster barrier would hold the peers: a CTA leaves only once every CTA
+    // of its cluster is done with them (a CTA whose wait gave up skips its epilogue and would
+    // otherwise leave first).
+    cluster.sync();
 }
 
 size_t persist_smem_bytes(int NT) {
@@ -843,6 +851,9 @@ cudaError_t launch_dense_persistent(const Graph& g, const StepArgs& sa, uint8_t*
     pa.step_begin = b;
     pa.step_end = e;
     pa.done = done;
+    const TestFault tf = test_fault("dense", 1ll << 31);
+    pa.wait_cycles = tf.wait_cycles;
+    pa.withhold = tf.withhold;
     const size_t smem = persist_smem_bytes(a.NT);
     cudaError_t ce = cudaFuncSetAttribute(dense_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);

@@ -100,10 +100,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
     const long long start = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - start > kWaitBudget) return false;
+        if (clock64() - start > budget) return false;
     }
     return true;
 }
@@ -235,6 +235,8 @@ struct D4Args {
     uint32_t seed_lo, seed_hi, instance;
     int32_t offset_mode;
     int* err;
+    long long wait_cycles;    // clock64 budget of each mbarrier wait (about a second; shorter in tests)
+    int32_t withhold;         // test-only: CTA 0 of the first cluster never copies its slice to CTA 1
 };
 
 // Shared memory: J rows (64K), two buffers of the FP4 spin operand (K N / 2 each), per-row
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         const uint8_t* gB = a.B0 + (size_t)g * bytesB;
         for (uint32_t off = 0; off < bytesB; off += 65536u)
             bulk_g2s(sB0 + off, gB + off, min(65536u, bytesB - off), bar_b0);
-        if (!mbar_wait_bounded(bar_j, 0)) {
+        if (!mbar_wait_bounded(bar_j, 0, a.wait_cycles)) {
             atomicExch(a.err, 11);
             s_abort = 1;
         }
@@ -371,8 +373,8 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
             if (lane == 0) {
                 ok = s_abort == 0 ? 1u : 0u;
                 // step 0 reads the start spins; step ls >= 1 the C slices of buffer ls & 1
-                if (ok) ok = (ls == 0 ? mbar_wait_bounded(bar_b0, 0)
-                                      : mbar_wait_bounded(&full[buf], (uint32_t)(((ls - 1) >> 1) & 1))) ? 1u : 0u;
+                if (ok) ok = (ls == 0 ? mbar_wait_bounded(bar_b0, 0, a.wait_cycles)
+                                      : mbar_wait_bounded(&full[buf], (uint32_t)(((ls - 1) >> 1) & 1), a.wait_cycles)) ? 1u : 0u;
                 if (ok) {
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB0 + (size_t)buf * bytesB);
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         }
         // ---- epilogue: wait (bounded) for this step's MMAs; the outcome is made uniform per warp
         uint32_t okw = 1;
-        if (lane == 0) okw = mbar_wait_bounded(bar_mma, (uint32_t)(ls & 1)) ? 1u : 0u;
+        if (lane == 0) okw = mbar_wait_bounded(bar_mma, (uint32_t)(ls & 1), a.wait_cycles) ? 1u : 0u;
         okw = __shfl_sync(0xFFFFFFFFu, okw, 0);
         if (!okw) {
             good = false;
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
             const uint8_t* src = dstB + rank * slice;
             if (lane == 0) {
                 mbar_arrive_expect_tx(nfull, slice * (uint32_t)(C - 1));
-            } else if (lane < C) {
+            } else if (lane < C && !(a.withhold && g == 0 && rank == 0 && lane == 1)) {
                 const uint32_t peer = (rank + (uint32_t)lane) % (uint32_t)C;
                 bulk_s2peer(map_rank(smem_u32(src), peer), src, slice, map_rank(smem_u32(nfull), peer));
             }
@@ -696,6 +698,9 @@ cudaError_t launch_dense4(const Graph& g, const StepArgs& sa, const int8_t* s_in
     a.instance = sa.instance;
     a.offset_mode = sa.offset_mode;
     a.err = g.err;
+    const TestFault tf = test_fault("dense4", kWaitBudget);
+    a.wait_cycles = tf.wait_cycles;
+    a.withhold = tf.withhold;
     return N == 48 ? launch_d4<48>(a, st) : launch_d4<32>(a, st);
 }
 

@@ -42,6 +42,8 @@ struct FlowArgs {
     unsigned* step_done;   // [k] tiles that finished step j
     unsigned long long* next;
     int* err;
+    long long wait_cycles;  // clock64 budget of each dependency wait (about 2 s; shorter in tests)
+    int withhold;           // test-only: tile 0 never publishes its progress
 };
 
 constexpr long long kFlowWaitCycles = 1ll << 32;  // about 2 s at 2 GHz
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowA
             if (d1 == d0) {
                 if (lane == 0)
                     while (flow_ld_acquire(f.step_done + (j - 1)) < (unsigned)f.ntiles)
-                        if (clock64() - start > kFlowWaitCycles) {
+                        if (clock64() - start > f.wait_cycles) {
                             ok = false;
                             break;
                         }
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowA
                 for (int d = d0 + lane; d < d1 && ok; d += 32) {
                     const unsigned* p = f.tile_done + __ldg(f.dep_idx + d);
                     while (flow_ld_acquire(p) < (unsigned)j)
-                        if (clock64() - start > kFlowWaitCycles) {
+                        if (clock64() - start > f.wait_cycles) {
                             ok = false;
                             break;
                         }
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowA
         if constexpr (WARP) process_tile_warp<G>(a, (uint32_t)t * (uint32_t)kBlock);
         else process_tile<G, UNIT, TABLE>(a, (int64_t)t * kBlock, s_tab);
         __syncthreads();  // every spin store of the tile precedes the release below
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !(f.withhold && t == 0)) {
             flow_st_release(f.tile_done + t, (unsigned)(j + 1));
             flow_red_release_add(f.step_done + j, 1u);
         }
@@ -249,6 +251,9 @@ cudaError_t launch_sparse_flow(const Graph& g, StepArgs a, int32_t k, const int8
     f.tile_done = tile_done;
     f.step_done = step_done;
     f.next = next;
+    const TestFault tf = test_fault("flow", kFlowWaitCycles);
+    f.wait_cycles = tf.wait_cycles;
+    f.withhold = tf.withhold;
     f.err = g.err;
     const int dev = g.device;
     if (v.warp_g != 0 && G == 32) return launch_flow_g<32, true, false, false>(f, dev, s);

@@ -143,6 +143,17 @@ struct StepArgs {
 // with l = ceil(log2 d); the quotient is exact for every 32-bit dividend below 2^31).
 void set_group_divisor(StepArgs& a, int32_t G);
 
+// Test-only fault switch, off by default and read on every launch: PBIT_TEST_WITHHOLD names one
+// persistent kernel ("flow", "batch", "dense" or "dense4") that then never publishes one of its
+// progress signals (a software flag, counter or slice copy that peers poll), and PBIT_TEST_WAIT_US
+// shortens that kernel's bounded waits to about the given microseconds, so a test can make a real
+// wait run out quickly and check PBIT_E_TIMEOUT without faulting the GPU.
+struct TestFault {
+    int withhold = 0;          // 1: this kernel withholds its designated signal
+    long long wait_cycles = 0; // clock64 budget of every bounded wait
+};
+TestFault test_fault(const char* kernel, long long default_cycles);
+
 // kernels (pbit_sparse.cu)
 cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t instance, int8_t* spins,
                               cudaStream_t s);
