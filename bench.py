@@ -547,17 +547,37 @@ def run_single(args, w, variant, kernel, dense, steps, warmup, e2e_reps, dist, w
 
 # ---------------------------------------------------------------- batch ----
 
+def batch_variant_kw(args, w) -> dict:
+    """make_params keywords of the pSA variant / timing model chosen on the command line for one batch
+    instance (empty for plain pSA)."""
+    from paper_2601_14476_gb300 import pbit
+    alg = {"psa": pbit.ALG_PSA, "spsa": pbit.ALG_SPSA, "tapsa": pbit.ALG_TAPSA}[args.algorithm]
+    if alg == pbit.ALG_PSA and args.t_res <= 0:
+        return {}
+    out = {"algorithm": alg, "stall_prob": args.stall_prob, "window": args.window}
+    if args.t_res > 0:
+        out["t_res"] = args.t_res
+        out["nu_dev"] = inputs.timing_deviation(w.graph.n, w.seed * 1000 + w.instance, args.s_nu)
+    return out
+
+
 def run_batch(args, ws, Gs, wname, dist, world, local):
     """The batched persistent form (timed `args.steps` times) against the plain one-instance-per-launch
-    form of the same work on the same GPU; results must be identical per trial."""
+    form of the same work on the same GPU; results must be identical per trial.  With a pSA variant
+    chosen, every instance runs it, and the batched form is also timed with the variants kept in the
+    group tile (the word tile's gain)."""
     import torch
     from paper_2601_14476_gb300 import pbit
     pk = peaks()
     stream = torch.cuda.current_stream()
+    vkw = [batch_variant_kw(args, w) for w in ws]
     kws = [dict(trials=w.trials, steps=w.steps, seed=w.seed, instance=w.instance, variability=w.var,
-                i0_min=w.c_min, i0_max=w.c_max) for w in ws]
-    upd_run = sum(w.graph.n * w.trials * w.steps for w in ws)
-    bytes_run = sum(w.graph.n * w.trials * w.steps * (2.0 * w.graph.m / w.graph.n + 2.0) for w in ws)
+                i0_min=w.c_min, i0_max=w.c_max, **v) for w, v in zip(ws, vkw)]
+    work = [variant_work(v, w.graph, w.trials, w.steps * max(1, v.get("t_res", 0))) if v else
+            (w.graph.n * w.trials * w.steps, w.graph.n * w.trials * w.steps * (2.0 * w.graph.m / w.graph.n + 2.0))
+            for w, v in zip(ws, vkw)]
+    upd_run = sum(x[0] for x in work)
+    bytes_run = sum(x[1] for x in work)
     B0 = pbit.Batch(Gs, kws)
     tuning = B0.autotune(stream)
     B0.close()
@@ -611,6 +631,29 @@ def run_batch(args, ws, Gs, wname, dist, world, local):
     plain_value, plain_ms = job_throughput(dist, upd_run, float(np.mean(plain_ms_all)), world)
     plain_cuts = [G.cut(o) for G, o in zip(Gs, outs)]
     same = all(np.array_equal(x, y) for x, y in zip(batched_cuts, plain_cuts))
+    group = None
+    if any(vkw):
+        # the same batch with the variants kept in the group tile (the switch is read at instance setup)
+        os.environ["PBIT_BATCH_GROUP_TILE"] = "1"
+        try:
+            gms = []
+            for it in range(1 + max(1, args.plain_reps)):
+                B = batched_run()
+                flush.zero_()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                B.run(stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if it >= 1:
+                    gms.append(a.elapsed_time(b))
+                gcuts = [B.cuts(k) for k in range(len(ws))]
+                B.close()
+        finally:
+            os.environ.pop("PBIT_BATCH_GROUP_TILE", None)
+        group = {"group_tile_ms": float(np.mean(gms)), "word_tile_over_group_tile": float(np.mean(gms)) / ms,
+                 "cuts_identical": all(np.array_equal(x, y) for x, y in zip(batched_cuts, gcuts))}
     # end to end: graphs from host arrays, batch setup, run, cuts back to host
     e2e = []
     for it in range(0 if args.no_e2e else 2):
@@ -634,7 +677,7 @@ def run_batch(args, ws, Gs, wname, dist, world, local):
     achieved = bytes_run / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"],
-                "traffic": batch_traffic(tuning, ws[0].steps) if wname.startswith("batch") else None,
+                "traffic": batch_traffic(tuning, ws[0].steps) if wname.startswith("batch") and not any(vkw) else None,
                 "kernel": "batch_chunk_kernel", "peak_source": pk["source"],
                 "per_launch": "sum over instances of (deg+2) bytes x n*T updates per step, over the "
                               "batched run's chunk launches",
@@ -643,7 +686,7 @@ def run_batch(args, ws, Gs, wname, dist, world, local):
             "plain_ms": plain_ms, "batched_over_plain": plain_ms / ms, "cuts_identical_to_plain": bool(same),
             "mean_cut_batched": float(np.mean([c.mean() for c in batched_cuts])),
             "mean_cut_plain": float(np.mean([c.mean() for c in plain_cuts])),
-            "batched_cuts": batched_cuts, "roofline": roofline, "launches": int(launches),
+            "batched_cuts": batched_cuts, "roofline": roofline, "launches": int(launches), "group_tile": group,
             "e2e": {"value": world * upd_run / float(np.mean(e2e)) if e2e else None, "unit": "spin-updates/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "clocks": clk.summary()}
@@ -796,7 +839,9 @@ def bench_multi(args):
             cfg.update({"tuning": b["tuning"], "l2": "flushed between timed steps", "plain_value": b["plain_value"],
                         "plain_ms": b["plain_ms"], "batched_over_plain": b["batched_over_plain"],
                         "cuts_identical_to_plain": b["cuts_identical_to_plain"],
-                        "mean_cut_batched": b["mean_cut_batched"], "mean_cut_plain": b["mean_cut_plain"]})
+                        "mean_cut_batched": b["mean_cut_batched"], "mean_cut_plain": b["mean_cut_plain"],
+                        "variant": {k: v for k, v in batch_variant_kw(args, ws[0]).items() if k != "nu_dev"} or None,
+                        "group_tile": b["group_tile"]})
             line = {"metric": "spin-updates/s", "value": b["value"], "unit": "spin-updates/s", "n_gpus": world,
                     "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None, "dtype": "i8/f32", "data": "synthetic", "config": cfg,

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -42,6 +43,8 @@ struct InstDesc {
     int32_t tiles;     // tiles per step
     int32_t active;    // 0 = slot unused
     int32_t T_real;    // trials the caller asked for; a.T is the padded row stride
+    int32_t words;     // 1: SpSA / TApSA in the coalesced word tile (a.T % 128 == 0, no timing model)
+    int32_t spans;     // word tile: 128-trial spans per node
 };
 
 struct ChunkArgs {
@@ -95,6 +98,40 @@ __device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int
     }
 }
 
+// SpSA and TApSA in the word tile for one batch tile: warp w of the block takes the (node, 128-trial
+// span) units (tile * 8 + w) * 4 .. + 3 (an item then holds as many updates as a group-tile item).
+constexpr int kWordUnits = 4;  // (node, span) units per warp and item: an item holds 4096 updates
+
+template <bool UNIT>
+__device__ void batch_words_unit(const StepArgs& a, int spans, int64_t lw);
+
+template <bool UNIT>
+__device__ void batch_words_tile(const StepArgs& a, int spans, int tile_i) {
+    const int warp = (int)(threadIdx.x >> 5);
+    for (int u = 0; u < kWordUnits; ++u)
+        batch_words_unit<UNIT>(a, spans, ((int64_t)tile_i * (kBlock / 32) + warp) * kWordUnits + u);
+}
+
+template <bool UNIT>
+__device__ void batch_words_unit(const StepArgs& a, int spans, int64_t lw) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int i = (int)(lw / spans);
+    if (i >= a.n) return;  // uniform across the warp
+    const int tb = (int)(lw - (int64_t)i * spans) * 128 + 4 * lane;
+    const uint32_t q = (uint32_t)a.step;
+    const float I0 = __ldg(a.i0_table + q);
+    const int hi = a.h ? __ldg(a.h + i) : 0;
+    const float lam = a.par.lambda ? __ldg(a.par.lambda + i) : 1.0f;
+    const float del = a.par.delta ? __ldg(a.par.delta + i) : 0.0f;
+    const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
+    const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+    const auto nbr = [&](int) -> const int8_t* { return a.in; };
+    if (a.alg == 2 && a.window == 4)
+        variant_words<1, UNIT, 4>(a, i, tb, I0, hi, lam, del, thr, rb, re, a.in, a.out, nbr, lane);
+    else
+        variant_words<1, UNIT, 0>(a, i, tb, I0, hi, lam, del, thr, rb, re, a.in, a.out, nbr, lane);
+}
+
 // VARIANTS = false: plain pSA only (the SpSA / TApSA / timing-model tiles are not compiled in,
 // which keeps the register count, and so the residency, of the common case).
 constexpr int kBatchMinBlocks = 8;
@@ -144,7 +181,16 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_
         const int par = (d.parity + k) & 1;
         a.in = d.buf[par];
         a.out = d.buf[par ^ 1];
-        dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
+        if constexpr (VARIANTS) {
+            if (d.words) {
+                if (d.unit) batch_words_tile<true>(a, d.spans, tile_i);
+                else batch_words_tile<false>(a, d.spans, tile_i);
+            } else {
+                dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
+            }
+        } else {
+            dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
+        }
         __threadfence();  // this thread's spin stores, before the tile is counted
         __syncthreads();
         if (threadIdx.x == 0 && !(c.withhold && g == 0 && k == 0 && tile_i == 0)) atomicAdd(c.tiles_done + g, 1u);
@@ -332,6 +378,17 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     d.table = v.table ? 1 : 0;
     const int64_t items = (int64_t)g.n * (T_pad / d.G);
     d.tiles = (int32_t)((items + kBlock - 1) / kBlock);
+    // SpSA and TApSA take the coalesced word tile when the padded rows hold whole 128-trial spans
+    // (measured on the 64-instance batch: 1.06x and 1.03x the group tile's rate); the timing model
+    // stays in the group tile, whose idle-node copies ran 1.2x faster there.  PBIT_BATCH_GROUP_TILE,
+    // read at every instance setup, keeps every variant in the group tile (comparisons).
+    d.words = a.alg != PBIT_ALG_PSA && a.t_res == 0 && T_pad % 128 == 0 &&
+              std::getenv("PBIT_BATCH_GROUP_TILE") == nullptr ? 1 : 0;
+    if (d.words) {
+        d.spans = T_pad / 128;
+        const int64_t per_tile = (kBlock / 32) * kWordUnits;
+        d.tiles = (int32_t)(((int64_t)g.n * d.spans + per_tile - 1) / per_tile);
+    }
     d.active = 1;
     return PBIT_OK;
 }
@@ -494,8 +551,10 @@ void pbit_batch_destroy(pbit_batch b) { delete b; }
 pbit_status pbit_batch_set_spins(pbit_batch b, int32_t k, const int8_t* spins, void* stream) {
     if (!b || k < 0 || k >= b->count || !spins) return fail(PBIT_E_INVALID, "batch_set_spins: bad argument");
     InstDesc& d = b->host_desc[(size_t)k];
-    PBIT_CUDA_TRY(cudaMemcpy2DAsync(d.buf[d.parity], (size_t)d.a.T, spins, (size_t)d.T_real, (size_t)d.T_real,
-                                    (size_t)d.a.n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    // both buffers, so the output buffer of the next step never holds a state older than this one
+    for (int q = 0; q < 2; ++q)
+        PBIT_CUDA_TRY(cudaMemcpy2DAsync(d.buf[q], (size_t)d.a.T, spins, (size_t)d.T_real, (size_t)d.T_real,
+                                        (size_t)d.a.n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return PBIT_OK;
 }
 

@@ -468,5 +468,148 @@ __device__ __forceinline__ void process_tile_variant(const StepArgs& a, int64_t 
     store_group<G>(a.out + (size_t)i * a.T + t0, neww);
 }
 
+
+// The variants' coalesced word tile, the work of one warp (shared by the one-step variant kernel and the
+// batched chunk kernel): node i, trials tb + 128 k of the word span (tb = span start + 4 lane), its
+// spins read from `src` and written to `dst`, neighbour e's spins read from nbr(e); I0, the node's
+// parameters and its CSR row [rb, re) already loaded.  Every lane of the warp works on node i (the
+// threshold table below is shuffled across the warp).
+__device__ __forceinline__ uint32_t wld32(const int8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ void wst32(int8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+
+template <int NW, bool UNIT, int WIN, typename Nbr>
+__device__ __forceinline__ void variant_words(const StepArgs& a, int i, int tb, float I0, int hi, float lam, float del,
+                                              uint32_t thr, int rb, int re, const int8_t* src, int8_t* dst, Nbr nbr,
+                                              int lane) {
+    const int T = a.T;
+    const uint32_t q = (uint32_t)a.step;
+    const size_t row = (size_t)i * T;
+    // the carried state first, so that its loads are in flight during the gather:
+    // SpSA the last inputs, TApSA the sum of the ring slots other than q % window
+    const size_t plane = (size_t)a.n * T;
+    const int slot = a.alg == 2 ? (int)(q % (uint32_t)a.window) : 0;
+    float4 prev[NW];
+    int osum[4 * NW];
+#pragma unroll
+    for (int k = 0; k < 4 * NW; ++k) osum[k] = 0;
+    if (a.alg == 1) {
+#pragma unroll
+        for (int k = 0; k < NW; ++k) prev[k] = *reinterpret_cast<const float4*>(a.Iprev + row + tb + 128 * k);
+    } else if (a.alg == 2) {
+        const auto add_slot = [&](int w) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const uint2 v = *reinterpret_cast<const uint2*>(a.ring + (size_t)w * plane + row + tb + 128 * k);
+                osum[4 * k] += (int)(int16_t)(v.x & 0xFFFFu);
+                osum[4 * k + 1] += (int)(int16_t)(v.x >> 16);
+                osum[4 * k + 2] += (int)(int16_t)(v.y & 0xFFFFu);
+                osum[4 * k + 3] += (int)(int16_t)(v.y >> 16);
+            }
+        };
+        if constexpr (WIN > 0) {
+#pragma unroll
+            for (int u = 1; u < WIN; ++u) add_slot(slot + u < WIN ? slot + u : slot + u - WIN);
+        } else {
+            for (int u = 1; u < a.window; ++u) add_slot(slot + u < a.window ? slot + u : slot + u - a.window);
+        }
+    }
+    // exact fields D = h_i + sum_j J_ij s_j (Eq. 1)
+    int D[4 * NW];
+    uint32_t cnt2[NW];  // +-1 weights: per trial byte, 2 per neighbour with J_ij s_j = -1
+    if constexpr (UNIT) {
+        // bit 1 of the spin byte is set for -1; flipped for J = -1
+#pragma unroll
+        for (int k = 0; k < NW; ++k) cnt2[k] = 0;
+        for (int e = rb; e < re; ++e) {
+            const int8_t* pj = nbr(e) + (size_t)__ldg(a.col + e) * T + tb;
+            const uint32_t flip = __ldg(a.J + e) < 0 ? 0x02020202u : 0u;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) cnt2[k] += (wld32(pj + 128 * k) & 0x02020202u) ^ flip;
+        }
+        const int base = hi + (re - rb);
+#pragma unroll
+        for (int k = 0; k < NW; ++k)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) D[4 * k + b] = base - (int)((cnt2[k] >> (8 * b)) & 0xFFu);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4 * NW; ++k) D[k] = hi;
+        for (int e = rb; e < re; ++e) {
+            const int8_t* pj = nbr(e) + (size_t)__ldg(a.col + e) * T + tb;
+            const int w = __ldg(a.J + e);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const uint32_t v = wld32(pj + 128 * k);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) D[4 * k + b] += w * sbyte(v, b);
+            }
+        }
+    }
+    // pSA under the timing model with +-1 weights and degree <= 15: the input depends on the count
+    // alone, so lane c (every lane of the warp has node i) computes the threshold of count c once and
+    // each trial reads its own with a shuffle; the same float operations as the per-trial form
+    bool table = false;
+    uint32_t negk_lane = 0;
+    if constexpr (UNIT) {
+        if (a.alg == 0 && 2 * (re - rb) + 1 <= 32) {
+            table = true;
+            const float Ic = __fmul_rn(I0, (float)(hi + (re - rb) - lane));  // counts above 2 deg are never read
+            negk_lane = 0u - pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, Ic));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const int t = tb + 128 * k;
+        const size_t cell = row + t;
+        float I[4];
+        if (a.alg == 1) {
+            // SpSA: stall draw of trial t + b = word b of Philox(node, q, t / 4, instance ^ 2^31)
+            const uint4 sw = philox((uint32_t)i, q, a.instance ^ 0x80000000u, (uint32_t)t >> 2, a.seed_lo, a.seed_hi);
+            I[0] = (sw.x >> 8) < a.stall_thr ? prev[k].x : __fmul_rn(I0, (float)D[4 * k]);
+            I[1] = (sw.y >> 8) < a.stall_thr ? prev[k].y : __fmul_rn(I0, (float)D[4 * k + 1]);
+            I[2] = (sw.z >> 8) < a.stall_thr ? prev[k].z : __fmul_rn(I0, (float)D[4 * k + 2]);
+            I[3] = (sw.w >> 8) < a.stall_thr ? prev[k].w : __fmul_rn(I0, (float)D[4 * k + 3]);
+            *reinterpret_cast<float4*>(a.Iprev + cell) = make_float4(I[0], I[1], I[2], I[3]);
+        } else if (a.alg == 2) {
+            // TApSA: ring slot q % window <- D (int16); I = I0 * (sum of the ring) / window
+            int16_t d16[4];
+            int sum[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                d16[b] = (int16_t)D[4 * k + b];
+                sum[b] = osum[4 * k + b] + d16[b];
+            }
+            *reinterpret_cast<uint2*>(a.ring + (size_t)slot * plane + cell) =
+                make_uint2((uint32_t)(uint16_t)d16[0] | ((uint32_t)(uint16_t)d16[1] << 16),
+                           (uint32_t)(uint16_t)d16[2] | ((uint32_t)(uint16_t)d16[3] << 16));
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                // sum / window: for the paper's window of 4 a multiply by 0.25, exact like the division
+                const float mean = WIN == 4 ? __fmul_rn((float)sum[b], 0.25f) : __fdiv_rn((float)sum[b], (float)a.window);
+                I[b] = __fmul_rn(I0, mean);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) I[b] = __fmul_rn(I0, (float)D[4 * k + b]);
+        }
+        // decisions (Eq. 6): candidate +1 iff r-word k-value < kthr, update iff u-word < thr
+        uint4 r0, r1;
+        philox_pair((uint32_t)i, q, a.instance, (uint32_t)t >> 1, (uint32_t)(t + 2) >> 1, a.seed_lo, a.seed_hi, r0,
+                    r1);
+        uint32_t nk[4];
+        if (table) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) nk[b] = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt2[k], b));
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) nk[b] = 0u - pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[b]));
+        }
+        const uint32_t S = sign_bytes((r0.x >> 8) + nk[0], (r0.z >> 8) + nk[1], (r1.x >> 8) + nk[2], (r1.z >> 8) + nk[3]);
+        const uint32_t U = sign_bytes((r0.y >> 8) - thr, (r0.w >> 8) - thr, (r1.y >> 8) - thr, (r1.w >> 8) - thr);
+        const uint32_t old = wld32(src + cell);
+        wst32(dst + cell, ((U & ~S) | (~U & old)) | 0x01010101u);
+    }
+}
+
 }  // namespace tile
 }  // namespace pbit

@@ -298,3 +298,30 @@ def test_variants_on_degenerate_graphs(alg):
         ref, _ = oracle.anneal_variant(csr, oracle.init_spins(n, T, 4), tab, 3, h=h, **kw)
         bad = whole != ref
         assert bad.sum() <= 1, (n, int(bad.sum()))
+
+
+def test_variants_in_batch_word_tile_equal_alone():
+    """Instances whose padded rows hold whole 128-trial spans run SpSA and TApSA in the batch through the
+    coalesced word tile (timing-model instances beside them in the group tile, chunk boundaries falling
+    inside their periods); each equals its own pbit_anneal run."""
+    gs = [inputs.erdos_renyi_gnm(700, 2100, 5, "+1"), inputs.rgg_knn(900, 6, 3, "pm1"),
+          inputs.torus_2d(20, 25, 7, "pm1"), inputs.torus_2d(24, 25, 8, "pm1"),
+          inputs.erdos_renyi_gnm(600, 1800, 9, "pm1")]
+    nu = np.random.default_rng(6).normal(0, 0.3, 900).astype(np.float32)
+    var = inputs.variability(900, 4, s_intensity=0.3, s_offset=0.3)
+    v5 = lambda n: {k: x[:n] for k, x in var.items()}  # noqa: E731
+    kws = [dict(trials=256, steps=45, seed=11, algorithm=pbit.ALG_SPSA, variability=v5(700)),
+           dict(trials=128, steps=37, seed=12, algorithm=pbit.ALG_TAPSA, window=4, variability=v5(900)),
+           dict(trials=128, steps=5, seed=13, t_res=10, nu_dev=nu[:500], algorithm=pbit.ALG_PSA),
+           dict(trials=256, steps=4, seed=14, t_res=10, nu_dev=nu[:600], algorithm=pbit.ALG_TAPSA, window=3,
+                variability=v5(600)),
+           dict(trials=128, steps=30, seed=15, algorithm=pbit.ALG_TAPSA, window=3, instance=7)]
+    Gs = [pbit.Graph.from_inputs(g) for g in gs]
+    B = pbit.Batch(Gs, kws)
+    B.run(chunk_steps=7)
+    for k, (G, kw) in enumerate(zip(Gs, kws)):
+        out = torch.empty((G.n, kw["trials"]), dtype=torch.int8, device="cuda")
+        p, keep = pbit.make_params(**kw)
+        pbit.pbit_anneal(G.handle, p, None, out)
+        assert np.array_equal(B.spins(k).cpu().numpy(), _host(out)), k
+    Gs[0].status()
