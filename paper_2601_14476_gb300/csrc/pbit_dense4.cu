@@ -19,11 +19,13 @@
 //   shared memory for the whole anneal (64K bytes: 128 KB at n = 2048) and two
 //   buffers of the group's spins in the MMA's B layout (K x N nibbles each).
 //   Per step:
-//     1. the control thread waits until all C slices of the step's spins
-//        have arrived in the current buffer, issues K/64 MMAs
-//        (M = 128, N, K = 64) into TMEM and commits them to an mbarrier;
+//     1. two issuing threads (one per MMA warp) wait until all C slices of
+//        the step's spins have arrived in the current buffer, each issues
+//        half of the K/64 MMAs (M = 128, N, K = 64; even / odd K chunks)
+//        into its own TMEM accumulator and commits them to one mbarrier;
 //     2. the epilogue warps (N/4 of them: warp w reads TMEM lanes 32(w%4)..
-//        and the 16 trial columns 16(w/4)..) take the p-bit decisions
+//        and the 16 trial columns 16(w/4).. of both accumulators, whose
+//        sum is exact) take the p-bit decisions
 //        (Eq. pbits_variability, timing draw; the Philox words and I0 were
 //        drawn during the previous step's copies and MMAs), pack the new
 //        spins of their 32 rows with warp ballots into this CTA's slice of
@@ -72,8 +74,9 @@ namespace {
 
 constexpr int kR = 128;                 // rows per CTA (MMA M)
 constexpr int kMaxC = 16;               // CTAs per cluster
-constexpr uint32_t kTmemCols = 128;     // accumulator (<= 64 columns) + scale factors
-constexpr uint32_t kSfaCol = 64, kSfbCol = 96;
+constexpr uint32_t kTmemCols = 256;     // two accumulators (<= 48 columns each) + scale factors
+constexpr uint32_t kD1Col = 64;         // second accumulator (odd K chunks)
+constexpr uint32_t kSfaCol = 128, kSfbCol = 160;
 constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;  // four UE8M0 scale factors equal to 2^0
 constexpr long long kWaitBudget = 1ll << 31;   // clock64 cycles (about a second) before a wait gives up
 
@@ -246,10 +249,12 @@ size_t d4_smem_bytes(int C, int N) {
     return 128 + 64 * K + K * (size_t)N + (size_t)kR * 16 + 8 * 5 + 16;
 }
 
-// Warps 0 .. E-1 (E = N/4: four lane quarters x N/16 groups of 16 trials) are the epilogue; warp E
-// is the control warp.
+// Warps 0 .. E-1 (E = N/4: four lane quarters x N/16 groups of 16 trials) are the epilogue; warps E
+// and E+1 issue the MMAs (even and odd K chunks into two accumulators: one thread issues a
+// tcgen05.mma only every 66-87 cycles, while the tensor core needs about 47 for M = 128, N = 48,
+// K = 64, so two issuers keep it busy).  Warp E also loads J.
 template <int N>
-__global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4Args a) {
+__global__ void __launch_bounds__((N / 4 + 2) * 32, 1) dense4_cluster_kernel(D4Args a) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int C = a.C;
@@ -272,7 +277,8 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
 
     constexpr int E = N / 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool control = warp == E;
+    const bool control = warp >= E;
+    const uint32_t issuer = control ? (uint32_t)(warp - E) : 0u;
     const uint32_t rank = cg::this_cluster().block_rank();
     const int g = blockIdx.y;
     const int L = a.step_end - a.step_begin;
@@ -284,8 +290,8 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (control && lane == 0) {
-        for (int k = 0; k < 5; ++k) mbar_init(&full[k], 1);
+    if (warp == E && lane == 0) {
+        for (int k = 0; k < 5; ++k) mbar_init(&full[k], &full[k] == bar_mma ? 2u : 1u);  // two MMA commits
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
     cluster_sync_all();
     tc_fence_after();
 
-    if (control && lane == 0) {
+    if (warp == E && lane == 0) {
         // J rows of this CTA (stationary) and the group's start spins
         mbar_arrive_expect_tx(bar_j, bytesA);
         const uint8_t* gA = a.J4 + (size_t)rank * bytesA;
@@ -368,20 +374,26 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
     for (int ls = 0; ls < mma_steps; ++ls) {
         const int buf = ls & 1;
         if (control) {
-            // only lane 0 issues; the control warp leaves the loop as a whole once a wait gave up
+            // lane 0 of each MMA warp issues; the warp leaves the loop as a whole once a wait gave up
             uint32_t ok = 1;
             if (lane == 0) {
                 ok = s_abort == 0 ? 1u : 0u;
+                // the second issuer checks for J itself (warp E waited for it before the loop)
+                if (ok && ls == 0 && issuer == 1) ok = mbar_wait_bounded(bar_j, 0, a.wait_cycles) ? 1u : 0u;
                 // step 0 reads the start spins; step ls >= 1 the C slices of buffer ls & 1
                 if (ok) ok = (ls == 0 ? mbar_wait_bounded(bar_b0, 0, a.wait_cycles)
                                       : mbar_wait_bounded(&full[buf], (uint32_t)(((ls - 1) >> 1) & 1), a.wait_cycles)) ? 1u : 0u;
                 if (ok) {
                     tc_fence_after();
+                    // K chunks issuer, issuer + 2, ... (K / 64 = 2C is even) into accumulator `issuer`; the
+                    // descriptors advance by two chunks (start address field in 16-byte units)
                     const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB0 + (size_t)buf * bytesB);
-                    for (uint32_t kk = 0; kk < K / 64; ++kk)
-                        mma_mxf4(tmem, smem_desc(a0 + kk * 2 * lboA, lboA, 128),
-                                 smem_desc(b0 + kk * 2 * lboB, lboB, 128), idesc, tmem + kSfaCol, tmem + kSfbCol,
-                                 kk > 0 ? 1u : 0u);
+                    const uint64_t dA = smem_desc(a0 + issuer * 2 * lboA, lboA, 128);
+                    const uint64_t dB = smem_desc(b0 + issuer * 2 * lboB, lboB, 128);
+                    const uint32_t d = tmem + issuer * kD1Col;
+                    for (uint32_t j = 0; j < K / 128; ++j)
+                        mma_mxf4(d, dA + (uint64_t)(j * (lboA >> 2)), dB + (uint64_t)(j * (lboB >> 2)), idesc,
+                                 tmem + kSfaCol, tmem + kSfbCol, j > 0 ? 1u : 0u);
                     mma_commit(bar_mma);
                 } else if (s_abort == 0) {
                     atomicExch(a.err, 12);
@@ -401,8 +413,13 @@ __global__ void __launch_bounds__((N / 4 + 1) * 32, 1) dense4_cluster_kernel(D4A
         uint32_t v[16];
         if (okw) {
             tc_fence_after();
+            uint32_t v1[16];
             tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + kD1Col + (uint32_t)c0, v1);
             tmem_wait_ld();
+            // the two partial sums are integers below 2^14 in magnitude: the float sum is exact
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[j]), __uint_as_float(v1[j])));
         }
         tc_fence_before();
         if (fields_only) {
@@ -619,7 +636,7 @@ static cudaError_t d4_config(int C, cudaLaunchConfig_t& cfg, cudaLaunchAttribute
         ce = cudaFuncSetAttribute(dense4_cluster_kernel<N>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (ce != cudaSuccess) return ce;
     }
-    cfg.blockDim = dim3((unsigned)(N / 4 + 1) * 32, 1, 1);
+    cfg.blockDim = dim3((unsigned)(N / 4 + 2) * 32, 1, 1);
     cfg.dynamicSmemBytes = smem;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)C;
