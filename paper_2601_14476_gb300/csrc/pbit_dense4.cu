@@ -30,18 +30,28 @@
 //        drawn during the previous step's copies and MMAs), pack the new
 //        spins of their 32 rows with warp ballots into this CTA's slice of
 //        the other buffer (64N bytes), and
-//     3. C-1 lanes copy that slice into the same place in the other C-1
-//        CTAs' buffers with cp.async.bulk shared::cta -> shared::cluster,
-//        each copy completing on the receiver's mbarrier (bytes counted).
-//   A CTA's next step therefore waits only for the C-1 copies of its own
-//   cluster; no global memory is touched between the first and last step.
+//     3. one thread stores that slice into a global staging slot (it stays
+//        in L2) and loads it back with one multicast bulk load into the
+//        same place of the other C-1 CTAs' buffers, completing on each
+//        receiver's mbarrier (bytes counted).
+//   A CTA's next step therefore waits only for the C-1 slices of its own
+//   cluster; J and the spins stay in shared memory, and the only memory
+//   traffic between the first and last step is the 64N-byte slice staging.
 //   The spins of a step are written to the buffer the step does not read,
 //   and a peer can only write a buffer again after this CTA's MMAs on it
-//   have completed (its copy depends on this CTA's next slice), so two
-//   buffers suffice.  Measured step anatomy (K_2000, 48 trials per cluster,
-//   cycles of one CTA): 32 MMAs 2.8K (about 87 cycles each whatever N is),
-//   TMEM read 0.3K, decisions 2.9K, ballot packing and the epilogue barrier
-//   1.1K, slice copies 3.2K, about 10.6K in all.
+//   have completed (its slice depends on this CTA's next slice), so two
+//   buffers suffice; for the same reason a staging slot is reused only
+//   after every peer has received what it held.  Measured step anatomy
+//   (K_2000, 48 trials per cluster, cycles of one CTA, clock64 marks):
+//   waiting for the slices 1.2K after the epilogue, 32 MMAs from two
+//   issuers 1.5-2.2K (about 47 cycles of tensor time each at N = 48; the
+//   issuers share their schedulers with the Philox draws of the next step)
+//   and their tail 0.4K, TMEM read and decisions 3.3K, ballot packing and
+//   the epilogue barrier 1.1K: about 8.2K in all.  One thread issues a
+//   tcgen05.mma only every 66-87 cycles and a bulk copy about every 128,
+//   hence two MMA issuers and the multicast: with one issuer the MMAs took
+//   2.8K, and with C-1 shared::cta -> shared::cluster copies (45 KB into
+//   and out of each SM per step) the slices came 3.3K after the epilogue.
 //
 // Layouts (no-swizzle K-major core matrices of 8 rows x 16 bytes = 8 x 32
 // nodes; leading byte offset = distance of K-adjacent core matrices, stride
@@ -119,21 +129,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// Shared-memory address of the same variable in CTA `rank` of this cluster.
-__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-    return r;
+// Bulk store of `bytes` from this CTA's shared memory to global memory, waited for (the data is in
+// global memory when it returns).
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
-// Copy `bytes` of this CTA's shared memory into a peer's (cluster address), completing on the
-// peer's mbarrier (cluster address).
-__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, const void* src, uint32_t bytes,
-                                            uint32_t bar_cluster) {
-    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     dst_cluster),
-                 "r"(smem_u32(src)), "r"(bytes), "r"(bar_cluster)
-                 : "memory");
+// Bulk load from global memory into the same shared-memory offset `dst` of every CTA in `mask`, each
+// completing `bytes` on its barrier at offset `bar`.
+__device__ __forceinline__ void bulk_g2s_multicast(const void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                   uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -227,6 +241,7 @@ __device__ __forceinline__ uint4 pack_row(uint32_t neg) {
 struct D4Args {
     const uint8_t* J4;        // packed e2m1 J, C row blocks of 64K bytes
     const uint8_t* B0;        // packed e2m1 start spins, groups of K*N/2 bytes
+    uint8_t* stage;           // slice staging for the exchange: [group][buffer][rank] slices of 64N bytes
     const int8_t* s_in;       // int8 [n][T] start state (the old spins of the hold rule)
     int8_t* s_out;            // int8 [n][T] final state
     int32_t* fields_out;      // fields only: int32 [n][T] D = h + J s of the start state
@@ -239,7 +254,7 @@ struct D4Args {
     int32_t offset_mode;
     int* err;
     long long wait_cycles;    // clock64 budget of each mbarrier wait (about a second; shorter in tests)
-    int32_t withhold;         // test-only: CTA 0 of the first cluster never copies its slice to CTA 1
+    int32_t withhold;         // test-only: CTA 0 of the first cluster never sends its slice to CTA 1
 };
 
 // Shared memory: J rows (64K), two buffers of the FP4 spin operand (K N / 2 each), per-row
@@ -480,17 +495,20 @@ __global__ void __launch_bounds__((N / 4 + 2) * 32, 1) dense4_cluster_kernel(D4A
             good = false;
             break;
         }
-        if (warp == 0) {
-            // lane 0 makes the local arrival (the C-1 peers' copies complete on the same barrier);
-            // lanes 1 .. C-1 each copy this CTA's slice into one peer
+        if (warp == 0 && lane == 0) {
+            // This CTA's slice goes to the peers in two bulk operations: a store into its global staging
+            // slot (group, buffer, rank), then one load from there multicast into the same place of
+            // the C-1 peers' buffers, completing on each peer's barrier.  Measured against C-1
+            // shared::cta -> shared::cluster copies (45 KB leaving and entering each SM per step at
+            // K_2000, 48 trials): the slices are in 1.2K instead of 3.3K cycles after the epilogue.
             uint64_t* nfull = &full[nb];
             const uint8_t* src = dstB + rank * slice;
-            if (lane == 0) {
-                mbar_arrive_expect_tx(nfull, slice * (uint32_t)(C - 1));
-            } else if (lane < C && !(a.withhold && g == 0 && rank == 0 && lane == 1)) {
-                const uint32_t peer = (rank + (uint32_t)lane) % (uint32_t)C;
-                bulk_s2peer(map_rank(smem_u32(src), peer), src, slice, map_rank(smem_u32(nfull), peer));
-            }
+            mbar_arrive_expect_tx(nfull, slice * (uint32_t)(C - 1));  // the C-1 peers' slices
+            uint8_t* stage = a.stage + (((size_t)g * 2 + nb) * (size_t)C + rank) * slice;
+            bulk_s2g(stage, src, slice);
+            uint32_t mask = ((1u << C) - 1u) & ~(1u << rank);
+            if (a.withhold && g == 0 && rank == 0) mask &= ~2u;  // test-only: CTA 1 never gets this slice
+            bulk_g2s_multicast(src, stage, slice, nfull, (uint16_t)mask);
         }
         // I0 and the Philox words of the next step, drawn while the copies and the next MMAs run
         I0 = a.i0_table[step + 1];
@@ -619,11 +637,13 @@ static int dense4_group(const Graph& g, int32_t T) {
     return best;
 }
 
+// Scratch of one launch: the packed start spins (K N / 2 bytes per group), then the slice staging
+// (two buffers of C slices of 64N bytes per group: K N bytes).
 size_t dense4_spin_bytes(const Graph& g, int32_t T) {
     const int N = dense4_group(g, T);
     if (N == 0) return 0;
     const int groups = (T + N - 1) / N;
-    return (size_t)groups * (size_t)(kR * g.dense4.C) * (size_t)N / 2;
+    return (size_t)groups * (size_t)(kR * g.dense4.C) * (size_t)N * 3 / 2;
 }
 
 template <int N>
@@ -698,6 +718,7 @@ cudaError_t launch_dense4(const Graph& g, const StepArgs& sa, const int8_t* s_in
     D4Args a{};
     a.J4 = g.dense4.J4;
     a.B0 = b0_scratch;
+    a.stage = b0_scratch + (size_t)groups * K * N / 2;
     a.s_in = s_in;
     a.s_out = s_out;
     a.fields_out = fields_out;
