@@ -144,16 +144,25 @@ __device__ __forceinline__ uint32_t pbit_kthr(float t) {
     return (uint32_t)(c + (1 << 24)) >> 1;
 }
 
+// 2^a from the hardware approximation (ex2.approx.ftz.f32).  For the
+// arguments pbit_kthr_of_x passes (|a| <= 57.71: no subnormal results) it
+// returned exactly exp2f's value on every float32 tried on GB300.
+__device__ __forceinline__ float pbit_exp2(float a) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
 // Decision threshold straight from x.  With t = tanh(x) = 1 - 2/(1 + e^(2x))
 // and q = 2^25 / (1 + e^(2x)), t * 2^24 = 2^24 - q, so
 // ceil(t * 2^24) = 2^24 - floor(q) and kthr = (2^25 - floor(q)) / 2 (floor).
 // Evaluated in float32 with x clamped to [-20, 20] (tanh rounds to +-1 there)
-// and e^(2x) = 2^(x * 2/ln 2) from exp2f; the threshold it gives corresponds
-// to a tanh value within about 2e-7 of the exact one, well inside the 1e-6
-// band in which decisions may differ from the FP64 definition.
+// and e^(2x) = 2^(x * 2/ln 2); the threshold it gives corresponds to a tanh
+// value within about 2e-7 of the exact one, well inside the 1e-6 band in
+// which decisions may differ from the FP64 definition.
 __device__ __forceinline__ uint32_t pbit_kthr_of_x(float x) {
     const float xc = fminf(fmaxf(x, -20.0f), 20.0f);
-    const float e = exp2f(xc * 2.8853900817779268f);
+    const float e = pbit_exp2(xc * 2.8853900817779268f);
     const float q = __fdividef(33554432.0f, 1.0f + e);  // in [0, 2^25]
     return (33554432u - (uint32_t)q) >> 1;
 }
