@@ -40,7 +40,8 @@ struct InstDesc {
     int32_t end;       // stop before this step
     int32_t parity;    // buf[parity] holds the state at `cur`
     int32_t G, unit, table;
-    int32_t tiles;     // tiles per step
+    int32_t tiles;     // work items per step (each up to kTilesPerItem tiles)
+    int32_t blocks;    // tiles per step
     int32_t active;    // 0 = slot unused
     int32_t T_real;    // trials the caller asked for; a.T is the padded row stride
     int32_t words;     // 1: SpSA / TApSA in the coalesced word tile (a.T % 128 == 0, no timing model)
@@ -132,11 +133,17 @@ __device__ void batch_words_unit(const StepArgs& a, int spans, int64_t lw) {
         variant_words<1, UNIT, 0>(a, i, tb, I0, hi, lam, del, thr, rb, re, a.in, a.out, nbr, lane);
 }
 
+// Tiles per claimed work item: the claim, the instance lookup, the step wait and the completion
+// count are paid once per item.
+constexpr int kTilesPerItem = 2;
+
 // VARIANTS = false: plain pSA only (the SpSA / TApSA / timing-model tiles are not compiled in,
 // which keeps the register count, and so the residency, of the common case).
 constexpr int kBatchMinBlocks = 8;
+constexpr int kBatchMinBlocksVariants = 4;
 template <bool VARIANTS>
-__global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_chunk_kernel(ChunkArgs c) {
+__global__ void __launch_bounds__(kBlock, VARIANTS ? kBatchMinBlocksVariants : kBatchMinBlocks)
+    batch_chunk_kernel(ChunkArgs c) {
     __shared__ uint32_t s_tab[kTabMax];
     __shared__ unsigned s_item;
     __shared__ int s_ok;
@@ -181,19 +188,27 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? 1 : kBatchMinBlocks) batch_
         const int par = (d.parity + k) & 1;
         a.in = d.buf[par];
         a.out = d.buf[par ^ 1];
-        if constexpr (VARIANTS) {
-            if (d.words) {
-                if (d.unit) batch_words_tile<true>(a, d.spans, tile_i);
-                else batch_words_tile<false>(a, d.spans, tile_i);
+        const int b_end = min(d.blocks, (tile_i + 1) * kTilesPerItem);
+        for (int b = tile_i * kTilesPerItem; b < b_end; ++b) {
+            if (b > tile_i * kTilesPerItem) __syncthreads();  // the previous tile's threshold table is read
+            if constexpr (VARIANTS) {
+                if (d.words) {
+                    if (d.unit) batch_words_tile<true>(a, d.spans, b);
+                    else batch_words_tile<false>(a, d.spans, b);
+                } else {
+                    dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab);
+                }
             } else {
-                dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
+                dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab);
             }
-        } else {
-            dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)tile_i * kBlock, s_tab);
         }
-        __threadfence();  // this thread's spin stores, before the tile is counted
+        // every thread's spin stores are ordered before thread 0's by the barrier; thread 0's fence
+        // then releases them all at GPU scope before the item is counted
         __syncthreads();
-        if (threadIdx.x == 0 && !(c.withhold && g == 0 && k == 0 && tile_i == 0)) atomicAdd(c.tiles_done + g, 1u);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (!(c.withhold && g == 0 && k == 0 && tile_i == 0)) atomicAdd(c.tiles_done + g, 1u);
+        }
     }
 }
 
@@ -377,7 +392,7 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     d.unit = v.unit ? 1 : 0;
     d.table = v.table ? 1 : 0;
     const int64_t items = (int64_t)g.n * (T_pad / d.G);
-    d.tiles = (int32_t)((items + kBlock - 1) / kBlock);
+    d.blocks = (int32_t)((items + kBlock - 1) / kBlock);
     // SpSA and TApSA take the coalesced word tile when the padded rows hold whole 128-trial spans
     // (measured on the 64-instance batch: 1.06x and 1.03x the group tile's rate); the timing model
     // stays in the group tile, whose idle-node copies ran 1.2x faster there.  PBIT_BATCH_GROUP_TILE,
@@ -387,8 +402,9 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     if (d.words) {
         d.spans = T_pad / 128;
         const int64_t per_tile = (kBlock / 32) * kWordUnits;
-        d.tiles = (int32_t)(((int64_t)g.n * d.spans + per_tile - 1) / per_tile);
+        d.blocks = (int32_t)(((int64_t)g.n * d.spans + per_tile - 1) / per_tile);
     }
+    d.tiles = (d.blocks + kTilesPerItem - 1) / kTilesPerItem;
     d.active = 1;
     return PBIT_OK;
 }
