@@ -76,7 +76,7 @@ def sparse_tile_kernel(g, T: int, launches_per_anneal: float, steps: int) -> str
     fewer launches than steps, else the one-step kernel of the graph's tile form.
 
     Same rule as the library's tile choice: the warp-table tile needs unit weights and
-    2 * max degree + 1 lanes per node segment of min(32, T / G) lanes (G = 32 or 16).
+    max degree + 1 lanes per node segment of min(32, T / G) lanes (G = 32 or 16).
     """
     if steps >= 2 and launches_per_anneal < steps / 2:
         return "sparse_flow_kernel"
@@ -84,7 +84,7 @@ def sparse_tile_kernel(g, T: int, launches_per_anneal: float, steps: int) -> str
     if np.all(np.abs(g.w) == 1) and deg <= 15:
         for G in (32, 16):
             groups = T // G
-            if T % G == 0 and (groups % 32 == 0 or 32 % groups == 0) and 2 * deg + 1 <= min(32, groups):
+            if T % G == 0 and (groups % 32 == 0 or 32 % groups == 0) and deg + 1 <= min(32, groups):
                 return "sparse_warp_kernel"
     return "sparse_step_kernel"
 

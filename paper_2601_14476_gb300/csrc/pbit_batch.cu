@@ -46,6 +46,7 @@ struct InstDesc {
     int32_t T_real;    // trials the caller asked for; a.T is the padded row stride
     int32_t words;     // 1: SpSA / TApSA in the coalesced word tile (a.T % 128 == 0, no timing model)
     int32_t spans;     // word tile: 128-trial spans per node
+    int32_t warp;      // 1: plain pSA in the warp-table tile (G = 16 or 32 trials per thread)
 };
 
 struct ChunkArgs {
@@ -73,7 +74,13 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int64_t first, uint3
 }
 
 template <bool VARIANTS>
-__device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int64_t first, uint32_t* s_tab) {
+__device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int64_t first, uint32_t* s_tab,
+                              int warp) {
+    if (warp) {
+        if (G == 32) process_tile_warp<32>(a, (uint32_t)first);
+        else process_tile_warp<16>(a, (uint32_t)first);
+        return;
+    }
     if (VARIANTS && is_variant(a)) {
         if (G == 16) {
             if (unit) process_tile_variant<16, true>(a, first); else process_tile_variant<16, false>(a, first);
@@ -196,10 +203,10 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? kBatchMinBlocksVariants : k
                     if (d.unit) batch_words_tile<true>(a, d.spans, b);
                     else batch_words_tile<false>(a, d.spans, b);
                 } else {
-                    dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab);
+                    dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab, d.warp);
                 }
             } else {
-                dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab);
+                dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab, d.warp);
             }
         }
         // every thread's spin stores are ordered before thread 0's by the barrier; thread 0's fence
@@ -386,11 +393,18 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     d.end = se;
     d.parity = 0;
     d.G = T_pad % 16 == 0 ? 16 : 4;
-    set_group_divisor(d.a, d.G);
     d.T_real = T;
     const SparseVariant v = choose_sparse_variant(g, T_pad);
     d.unit = v.unit ? 1 : 0;
     d.table = v.table ? 1 : 0;
+    // plain pSA takes the warp-table tile where the single-anneal path would (unit weights, every
+    // node's deg + 1 thresholds within its lane segment)
+    const int wg = v.warp_g != 0 ? warp_tile_group(g, T_pad, true) : 0;
+    if (wg != 0 && T_pad % 16 == 0 && a.alg == PBIT_ALG_PSA && a.t_res == 0) {
+        d.warp = 1;
+        d.G = wg;
+    }
+    set_group_divisor(d.a, d.G);
     const int64_t items = (int64_t)g.n * (T_pad / d.G);
     d.blocks = (int32_t)((items + kBlock - 1) / kBlock);
     // SpSA and TApSA take the coalesced word tile when the padded rows hold whole 128-trial spans

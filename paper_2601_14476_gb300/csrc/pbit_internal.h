@@ -166,6 +166,9 @@ struct SparseVariant {
     int warp_g = 0;      // trials per thread of the warp-table tile (0: not used); see pbit_tile.cuh
 };
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T);
+// Trials per thread of the warp-table tile (32, 16, or 0: not applicable); `wide` for many
+// instances sharing the GPU (prefers 32 whenever it applies).
+int warp_tile_group(const Graph& g, int32_t T, bool wide);
 cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant v = SparseVariant());
 // Steps [a.step, a.step + k) of plain pSA in one persistent launch: step j reads in0 (j = 0), P (odd j)
 // or Q (even j >= 2) and writes P (even j) or Q (odd j).  Scratch: tile_done [ntiles], step_done [k]

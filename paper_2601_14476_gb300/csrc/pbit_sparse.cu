@@ -361,19 +361,30 @@ cudaError_t launch_init_spins(int32_t n, int32_t T, uint64_t seed, uint32_t inst
     return cudaGetLastError();
 }
 
-// Trials per thread of the warp-table tile for T trials (0: the tile does not apply).
-int warp_tile_group(const Graph& g, int32_t T) {
+// Trials per thread of the warp-table tile for T trials (0: the tile does not apply).  32 trials
+// per thread need fewer instructions per update than 16, but give half the threads: a single
+// instance takes 32 only when that still fills two waves of the multi-step launch's grid (6 blocks
+// of 256 threads per SM); a batch (`wide`) gets its parallelism from its other instances.
+int warp_tile_group(const Graph& g, int32_t T, bool wide) {
     if (!g.unit_weights || g.max_degree > 15) return 0;
+    int fit32 = 0, fit16 = 0;
     for (const int G : {32, 16}) {
         if (T % G != 0) continue;
         const int64_t groups = T / G;
         if (groups % 32 != 0 && 32 % groups != 0) continue;
         const int64_t L = groups >= 32 ? 32 : groups;
-        if (2 * (int64_t)g.max_degree + 1 > L) continue;
+        if ((int64_t)g.max_degree + 1 > L) continue;  // one lane per possible count
         if ((int64_t)g.n * groups >= (int64_t(1) << 31)) continue;
-        return G;
+        (G == 32 ? fit32 : fit16) = 1;
     }
-    return 0;
+    static const int64_t two_waves = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return 2 * (int64_t)(sms > 0 ? sms : 152) * 6 * kBlock;
+    }();
+    if (fit32 && (wide || !fit16 || (int64_t)g.n * (T / 32) >= two_waves)) return 32;
+    return fit16 ? 16 : 0;
 }
 
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T) {
@@ -381,7 +392,7 @@ SparseVariant choose_sparse_variant(const Graph& g, int32_t T) {
     static const bool plain = std::getenv("PBIT_SPARSE_PLAIN") != nullptr;  // force the plain variant
     if (plain) return v;
     static const bool no_warp = std::getenv("PBIT_SPARSE_NOWARP") != nullptr;  // force the block-table tile
-    v.warp_g = no_warp ? 0 : warp_tile_group(g, T);
+    v.warp_g = no_warp ? 0 : warp_tile_group(g, T, false);
     const int G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
     v.unit = g.unit_weights && g.max_degree <= 127 && G >= 4;
     // table when its entries stay within shared memory and cost well under one per update

@@ -271,9 +271,10 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
 // either part of one node's trials (T / G >= 32 groups per node) or several
 // whole nodes (T / G divides 32), so each node owns a segment of L lanes,
 // L = min(32, T / G).  Lane seg + c holds the negated threshold for the field
-// h_i + deg_i - c (c = 0..2 deg_i, needing 2 deg_i + 1 <= L), and the update
-// with packed count c2 = 2 * #(J_ij s_j = -1) reads it with one shuffle from
-// lane seg + c2 (the field is h_i + deg_i - c2).  No shared memory, no block
+// h_i + deg_i - 2c (c = 0..deg_i, needing deg_i + 1 <= L: the field of a node
+// with unit weights has the parity of its degree), and the update with
+// packed count c2 = 2 * #(J_ij s_j = -1) reads it with one shuffle from lane
+// seg + c2 / 2 (the field is h_i + deg_i - c2).  No shared memory, no block
 // barrier.
 //
 // Decisions without branches or multiplies: (w >> 8) - kthr is negative
@@ -302,7 +303,7 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
     const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
     const int deg = re - rb;
-    const uint32_t negk_lane = 0u - pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + deg - ell));
+    const uint32_t negk_lane = 0u - pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + deg - 2 * ell));
     uint32_t cnt2[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) cnt2[w] = 0;
@@ -333,12 +334,13 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
         uint4 r[2];
         r[0] = philox_tail(ph, (uint32_t)(t0 + 4 * w) >> 1, a.seed_lo, a.seed_hi);
         r[1] = philox_tail(ph, (uint32_t)(t0 + 4 * w + 2) >> 1, a.seed_lo, a.seed_hi);
+        const uint32_t cnt = cnt2[w] >> 1;  // every byte of cnt2 is even: halving keeps the bytes apart
         uint32_t dr[4], du[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             // the shuffle width L keeps the source lane inside this node's segment
-            const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt2[w], 2 * h), L);
-            const uint32_t q1 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt2[w], 2 * h + 1), L);
+            const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt, 2 * h), L);
+            const uint32_t q1 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt, 2 * h + 1), L);
             dr[2 * h] = (r[h].x >> 8) + q0;
             du[2 * h] = (r[h].y >> 8) - thr;
             dr[2 * h + 1] = (r[h].z >> 8) + q1;

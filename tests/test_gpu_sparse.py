@@ -317,7 +317,7 @@ def test_kernel_variants_agree(tmp_path):
 
 
 def _warp_tile_applies(g, T):
-    """The launch rule of the warp-table tile: unit weights, 2 max-degree + 1 lanes per node segment."""
+    """The launch rule of the warp-table tile: unit weights, max-degree + 1 lanes per node segment."""
     deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).max() if g.m else 0
     if np.any(np.abs(g.w) != 1) or deg > 15:
         return False
@@ -327,7 +327,7 @@ def _warp_tile_applies(g, T):
         groups = T // G
         if groups % 32 and 32 % groups:
             continue
-        if 2 * deg + 1 <= min(32, groups):
+        if deg + 1 <= min(32, groups):
             return True
     return False
 
