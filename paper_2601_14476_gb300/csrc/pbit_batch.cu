@@ -40,13 +40,15 @@ struct InstDesc {
     int32_t end;       // stop before this step
     int32_t parity;    // buf[parity] holds the state at `cur`
     int32_t G, unit, table;
-    int32_t tiles;     // work items per step (each up to kTilesPerItem tiles)
+    int32_t tiles;     // work items per step (each up to ChunkArgs::tpi tiles)
     int32_t blocks;    // tiles per step
     int32_t active;    // 0 = slot unused
     int32_t T_real;    // trials the caller asked for; a.T is the padded row stride
     int32_t words;     // 1: SpSA / TApSA in the coalesced word tile (a.T % 128 == 0, no timing model)
     int32_t spans;     // word tile: 128-trial spans per node
-    int32_t warp;      // 1: plain pSA in the warp-table tile (G = 16 or 32 trials per thread)
+    int32_t warp;      // 1: plain pSA in the warp-table tile in this chunk (G = 16 or 32 trials per thread)
+    int32_t base_G;    // trials per thread of the shared-table tile
+    int32_t wg_wide;   // warp-table tile under a heavy load: trials per thread (0: not applicable)
 };
 
 struct ChunkArgs {
@@ -55,6 +57,7 @@ struct ChunkArgs {
     int32_t count;
     int32_t total_tiles;
     int32_t K;
+    int32_t tpi;                 // tiles per work item (1 or 2: the kernel's TPI)
     unsigned* queue;             // item counter
     unsigned* tiles_done;        // [count] tiles finished in this chunk
     int* err;
@@ -73,10 +76,10 @@ __device__ __forceinline__ void run_tile(const StepArgs& a, int64_t first, uint3
     process_tile<G, UNIT, TABLE>(a, first, s_tab);
 }
 
-template <bool VARIANTS>
+template <bool VARIANTS, bool WARP>
 __device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int64_t first, uint32_t* s_tab,
                               int warp) {
-    if (warp) {
+    if (WARP && warp) {
         if (G == 32) process_tile_warp<32>(a, (uint32_t)first);
         else process_tile_warp<16>(a, (uint32_t)first);
         return;
@@ -140,15 +143,13 @@ __device__ void batch_words_unit(const StepArgs& a, int spans, int64_t lw) {
         variant_words<1, UNIT, 0>(a, i, tb, I0, hi, lam, del, thr, rb, re, a.in, a.out, nbr, lane);
 }
 
-// Tiles per claimed work item: the claim, the instance lookup, the step wait and the completion
-// count are paid once per item.
-constexpr int kTilesPerItem = 2;
-
 // VARIANTS = false: plain pSA only (the SpSA / TApSA / timing-model tiles are not compiled in,
-// which keeps the register count, and so the residency, of the common case).
+// which keeps the register count, and so the residency, of the common case).  TPI: tiles per work
+// item (ChunkArgs::tpi), a template parameter so that the one-tile form keeps its straight-line code
+// (a runtime loop over tiles cost 19 % of a lone request's latency).
 constexpr int kBatchMinBlocks = 8;
 constexpr int kBatchMinBlocksVariants = 4;
-template <bool VARIANTS>
+template <bool VARIANTS, int TPI>
 __global__ void __launch_bounds__(kBlock, VARIANTS ? kBatchMinBlocksVariants : kBatchMinBlocks)
     batch_chunk_kernel(ChunkArgs c) {
     __shared__ uint32_t s_tab[kTabMax];
@@ -195,27 +196,24 @@ __global__ void __launch_bounds__(kBlock, VARIANTS ? kBatchMinBlocksVariants : k
         const int par = (d.parity + k) & 1;
         a.in = d.buf[par];
         a.out = d.buf[par ^ 1];
-        const int b_end = min(d.blocks, (tile_i + 1) * kTilesPerItem);
-        for (int b = tile_i * kTilesPerItem; b < b_end; ++b) {
-            if (b > tile_i * kTilesPerItem) __syncthreads();  // the previous tile's threshold table is read
+        const int b_first = tile_i * TPI, b_end = min(d.blocks, b_first + TPI);
+#pragma unroll
+        for (int b = b_first; b < b_end; ++b) {
+            if (TPI > 1 && b > b_first) __syncthreads();  // the previous tile's threshold table is read
             if constexpr (VARIANTS) {
                 if (d.words) {
                     if (d.unit) batch_words_tile<true>(a, d.spans, b);
                     else batch_words_tile<false>(a, d.spans, b);
                 } else {
-                    dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab, d.warp);
+                    dispatch_tile<VARIANTS, (TPI > 1)>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab, d.warp);
                 }
             } else {
-                dispatch_tile<VARIANTS>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab, d.warp);
+                dispatch_tile<VARIANTS, (TPI > 1)>(a, d.G, d.unit, d.table, (int64_t)b * kBlock, s_tab, d.warp);
             }
         }
-        // every thread's spin stores are ordered before thread 0's by the barrier; thread 0's fence
-        // then releases them all at GPU scope before the item is counted
+        __threadfence();  // this thread's spin stores, before the item is counted
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (!(c.withhold && g == 0 && k == 0 && tile_i == 0)) atomicAdd(c.tiles_done + g, 1u);
-        }
+        if (threadIdx.x == 0 && !(c.withhold && g == 0 && k == 0 && tile_i == 0)) atomicAdd(c.tiles_done + g, 1u);
     }
 }
 
@@ -257,6 +255,7 @@ struct pbit_batch_s {
     // tuning
     int32_t chunk = 32;
     int32_t ctas_per_sm = 0;             // 0 = occupancy maximum
+    int32_t tpi = 1;                     // tiles per work item (plan_chunk)
     // captured chunk graph
     cudaGraphExec_t exec = nullptr;
     cudaStream_t exec_stream = nullptr;
@@ -276,6 +275,37 @@ struct pbit_batch_s {
 };
 
 namespace {
+
+// Tiling of one instance for a chunk: trials per thread and tiles per step (the word tile's tiles are
+// fixed), then work items of `tpi` tiles.  Results do not depend on it.
+void plan_inst(InstDesc& d, bool wide, int tpi) {
+    if (!d.words) {
+        d.warp = wide && d.wg_wide != 0 ? 1 : 0;  // the one-tile kernel has no warp-table tile
+        d.G = d.warp ? d.wg_wide : d.base_G;
+        set_group_divisor(d.a, d.G);
+        const int64_t items = (int64_t)d.a.n * (d.a.T / d.G);
+        d.blocks = (int32_t)((items + kBlock - 1) / kBlock);
+    }
+    d.tiles = (d.blocks + tpi - 1) / tpi;
+}
+
+// Tiling of a chunk over `count` instances on a grid of at most `max_grid` CTAs.  Under a heavy load
+// (at least 16 instances and four tiles per CTA and step) the warp-table tile takes 32 trials per
+// thread and an item
+// holds two tiles: fewer instructions and claims per update (the 64-instance batch: 146 -> 133 ms).
+// Under a light load (a few resident requests) the shared-table tile with 16 trials per thread and
+// one tile per item keep every instance's step spread over as many CTAs as possible, which sets its
+// latency (a lone request's p50 rose 19 % with two-tile items).  Returns the tiles per item.
+int plan_chunk(InstDesc* d, int32_t count, int max_grid) {
+    int64_t blocks = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        plan_inst(d[k], true, 1);
+        blocks += d[k].blocks;
+    }
+    const bool heavy = count >= 16 && blocks >= 4 * (int64_t)max_grid;
+    for (int32_t k = 0; k < count; ++k) plan_inst(d[k], heavy, heavy ? 2 : 1);
+    return heavy ? 2 : 1;
+}
 
 // Device state of one instance: schedule table, per-node parameters, two
 // spin buffers (initial state from Philox).  Allocations are appended to
@@ -392,21 +422,16 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
     d.cur = sb;
     d.end = se;
     d.parity = 0;
-    d.G = T_pad % 16 == 0 ? 16 : 4;
+    d.base_G = T_pad % 16 == 0 ? 16 : 4;
     d.T_real = T;
     const SparseVariant v = choose_sparse_variant(g, T_pad);
     d.unit = v.unit ? 1 : 0;
     d.table = v.table ? 1 : 0;
     // plain pSA takes the warp-table tile where the single-anneal path would (unit weights, every
-    // node's deg + 1 thresholds within its lane segment)
-    const int wg = v.warp_g != 0 ? warp_tile_group(g, T_pad, true) : 0;
-    if (wg != 0 && T_pad % 16 == 0 && a.alg == PBIT_ALG_PSA && a.t_res == 0) {
-        d.warp = 1;
-        d.G = wg;
+    // node's deg + 1 thresholds within its lane segment) when the chunk's load is heavy
+    if (v.warp_g != 0 && T_pad % 16 == 0 && a.alg == PBIT_ALG_PSA && a.t_res == 0) {
+        d.wg_wide = warp_tile_group(g, T_pad, true);
     }
-    set_group_divisor(d.a, d.G);
-    const int64_t items = (int64_t)g.n * (T_pad / d.G);
-    d.blocks = (int32_t)((items + kBlock - 1) / kBlock);
     // SpSA and TApSA take the coalesced word tile when the padded rows hold whole 128-trial spans
     // (measured on the 64-instance batch: 1.06x and 1.03x the group tile's rate); the timing model
     // stays in the group tile, whose idle-node copies ran 1.2x faster there.  PBIT_BATCH_GROUP_TILE,
@@ -418,7 +443,7 @@ pbit_status build_inst(const Graph& g, const pbit_anneal_params& pp, cudaStream_
         const int64_t per_tile = (kBlock / 32) * kWordUnits;
         d.blocks = (int32_t)(((int64_t)g.n * d.spans + per_tile - 1) / per_tile);
     }
-    d.tiles = (d.blocks + kTilesPerItem - 1) / kTilesPerItem;
+    plan_inst(d, false, 1);
     d.active = 1;
     return PBIT_OK;
 }
@@ -452,14 +477,19 @@ pbit_status dev_alloc(pbit_batch b, T** p, size_t count) {
 
 int chunk_occupancy(bool variants) {
     int occ = 0;
-    if (variants) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel<true>, kBlock, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel<false>, kBlock, 0);
+    if (variants) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel<true, 1>, kBlock, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_chunk_kernel<false, 1>, kBlock, 0);
     return occ;
 }
 
 void launch_chunk(bool variants, int grid, const ChunkArgs& c, cudaStream_t s) {
-    if (variants) batch_chunk_kernel<true><<<grid, kBlock, 0, s>>>(c);
-    else batch_chunk_kernel<false><<<grid, kBlock, 0, s>>>(c);
+    if (c.tpi == 2) {
+        if (variants) batch_chunk_kernel<true, 2><<<grid, kBlock, 0, s>>>(c);
+        else batch_chunk_kernel<false, 2><<<grid, kBlock, 0, s>>>(c);
+    } else {
+        if (variants) batch_chunk_kernel<true, 1><<<grid, kBlock, 0, s>>>(c);
+        else batch_chunk_kernel<false, 1><<<grid, kBlock, 0, s>>>(c);
+    }
 }
 
 int grid_for(pbit_batch b) {
@@ -494,6 +524,7 @@ pbit_status ensure_graph(pbit_batch b, cudaStream_t user) {
     c.count = b->count;
     c.total_tiles = b->total_tiles;
     c.K = b->chunk;
+    c.tpi = b->tpi;
     c.queue = b->d_ctl;
     c.tiles_done = b->d_ctl + 1;
     c.err = nullptr;
@@ -561,8 +592,14 @@ pbit_status pbit_batch_create(int32_t count, const pbit_graph* graphs, const pbi
         InstDesc& d = b->host_desc[(size_t)k];
         if ((st = build_inst(*g, params[k], s, b->allocs, d, nullptr)) != PBIT_OK) return st;
         b->variants = b->variants || is_variant(d.a);
-        b->tile_prefix[(size_t)k + 1] = b->tile_prefix[(size_t)k] + d.tiles;
     }
+    {
+        int sms = 0;
+        PBIT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+        b->tpi = plan_chunk(b->host_desc.data(), count, sms * std::max(1, chunk_occupancy(b->variants)));
+    }
+    for (int32_t k = 0; k < count; ++k)
+        b->tile_prefix[(size_t)k + 1] = b->tile_prefix[(size_t)k] + b->host_desc[(size_t)k].tiles;
     b->total_tiles = b->tile_prefix[(size_t)count];
     PBIT_CUDA_TRY(cudaMalloc((void**)&b->d_inst, sizeof(InstDesc) * (size_t)count));
     PBIT_CUDA_TRY(cudaMalloc((void**)&b->d_prefix, sizeof(int32_t) * ((size_t)count + 1)));
@@ -808,8 +845,17 @@ void server_loop(pbit_server_s* S) {
         desc.resize((size_t)count);
         prefix.assign((size_t)count + 1, 0);
         double upd = 0.0;
+        bool variants = false;
         for (int32_t k = 0; k < count; ++k) {
             desc[(size_t)k] = active[(size_t)k]->desc;
+            variants = variants || is_variant(desc[(size_t)k].a);
+        }
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
+        const int occ = chunk_occupancy(variants);
+        const int grid = std::max(1, sms * std::max(1, occ));
+        const int tpi = plan_chunk(desc.data(), count, grid);  // the resident load sets the tiling
+        for (int32_t k = 0; k < count; ++k) {
             prefix[(size_t)k + 1] = prefix[(size_t)k] + desc[(size_t)k].tiles;
             const InstDesc& d = desc[(size_t)k];
             upd += (double)d.a.n * d.a.T * std::min(S->chunk, d.end - d.cur);
@@ -824,18 +870,14 @@ void server_loop(pbit_server_s* S) {
         c.count = count;
         c.total_tiles = prefix[(size_t)count];
         c.K = S->chunk;
+        c.tpi = tpi;
         c.queue = S->d_ctl;
         c.tiles_done = S->d_ctl + 1;
         c.err = S->d_err;
         const TestFault tf = test_fault("batch", 1ll << 31);
         c.wait_cycles = tf.wait_cycles;
         c.withhold = tf.withhold;
-        bool variants = false;
-        for (int32_t k = 0; k < count; ++k) variants = variants || is_variant(desc[(size_t)k].a);
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device);
-        const int occ = chunk_occupancy(variants);
-        launch_chunk(variants, std::max(1, sms * std::max(1, occ)), c, S->stream);
+        launch_chunk(variants, grid, c, S->stream);
         count_launches(1);
         {
             // requests arriving meanwhile are prepared now and join at the next chunk
