@@ -80,8 +80,8 @@ template <bool VARIANTS, bool WARP>
 __device__ void dispatch_tile(const StepArgs& a, int G, int unit, int table, int64_t first, uint32_t* s_tab,
                               int warp) {
     if (WARP && warp) {
-        if (G == 32) process_tile_warp<32>(a, (uint32_t)first);
-        else process_tile_warp<16>(a, (uint32_t)first);
+        if (G == 32) process_tile_warp<32, true>(a, (uint32_t)first);
+        else process_tile_warp<16, true>(a, (uint32_t)first);
         return;
     }
     if (VARIANTS && is_variant(a)) {

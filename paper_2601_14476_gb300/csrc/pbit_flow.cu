@@ -60,7 +60,7 @@ __device__ __forceinline__ void flow_red_release_add(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int G, bool WARP, bool UNIT, bool TABLE>
+template <int G, int WARP, bool UNIT, bool TABLE>
 __global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowArgs f) {
     __shared__ uint32_t s_tab[TABLE ? kTabMax : 1];
     __shared__ unsigned long long s_item;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowA
         a.step = f.a.step + j;
         a.in = j == 0 ? f.in0 : ((j & 1) ? f.P : f.Q);
         a.out = (j & 1) ? f.Q : f.P;
-        if constexpr (WARP) process_tile_warp<G>(a, (uint32_t)t * (uint32_t)kBlock);
+        if constexpr (WARP != 0) process_tile_warp<G, WARP == 2>(a, (uint32_t)t * (uint32_t)kBlock);
         else process_tile<G, UNIT, TABLE>(a, (int64_t)t * kBlock, s_tab);
         __syncthreads();  // every spin store of the tile precedes the release below
         if (threadIdx.x == 0 && !(f.withhold && t == 0)) {
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kBlock, WARP ? 6 : 1) sparse_flow_kernel(FlowA
     }
 }
 
-template <int G, bool WARP, bool UNIT, bool TABLE>
+template <int G, int WARP, bool UNIT, bool TABLE>
 cudaError_t launch_flow_g(const FlowArgs& f, int device, cudaStream_t s) {
     // resident CTAs of this instantiation on each device, computed once (concurrent first calls store
     // the same value)
@@ -256,22 +256,25 @@ cudaError_t launch_sparse_flow(const Graph& g, StepArgs a, int32_t k, const int8
     f.withhold = tf.withhold;
     f.err = g.err;
     const int dev = g.device;
-    if (v.warp_g != 0 && G == 32) return launch_flow_g<32, true, false, false>(f, dev, s);
-    if (v.warp_g != 0 && G == 16) return launch_flow_g<16, true, false, false>(f, dev, s);
+    // WARP: 0 shared-table tile, 1 warp-table tile, 2 warp-table tile indexed by count / 2
+    if (v.warp_g != 0 && G == 32)
+        return v.warp_half ? launch_flow_g<32, 2, false, false>(f, dev, s) : launch_flow_g<32, 1, false, false>(f, dev, s);
+    if (v.warp_g != 0 && G == 16)
+        return v.warp_half ? launch_flow_g<16, 2, false, false>(f, dev, s) : launch_flow_g<16, 1, false, false>(f, dev, s);
     if (G == 16) {
-        if (v.unit && v.table) return launch_flow_g<16, false, true, true>(f, dev, s);
-        if (v.unit) return launch_flow_g<16, false, true, false>(f, dev, s);
-        if (v.table) return launch_flow_g<16, false, false, true>(f, dev, s);
-        return launch_flow_g<16, false, false, false>(f, dev, s);
+        if (v.unit && v.table) return launch_flow_g<16, 0, true, true>(f, dev, s);
+        if (v.unit) return launch_flow_g<16, 0, true, false>(f, dev, s);
+        if (v.table) return launch_flow_g<16, 0, false, true>(f, dev, s);
+        return launch_flow_g<16, 0, false, false>(f, dev, s);
     }
     if (G == 4) {
-        if (v.unit && v.table) return launch_flow_g<4, false, true, true>(f, dev, s);
-        if (v.unit) return launch_flow_g<4, false, true, false>(f, dev, s);
-        if (v.table) return launch_flow_g<4, false, false, true>(f, dev, s);
-        return launch_flow_g<4, false, false, false>(f, dev, s);
+        if (v.unit && v.table) return launch_flow_g<4, 0, true, true>(f, dev, s);
+        if (v.unit) return launch_flow_g<4, 0, true, false>(f, dev, s);
+        if (v.table) return launch_flow_g<4, 0, false, true>(f, dev, s);
+        return launch_flow_g<4, 0, false, false>(f, dev, s);
     }
-    if (v.table) return launch_flow_g<1, false, false, true>(f, dev, s);
-    return launch_flow_g<1, false, false, false>(f, dev, s);
+    if (v.table) return launch_flow_g<1, 0, false, true>(f, dev, s);
+    return launch_flow_g<1, 0, false, false>(f, dev, s);
 }
 
 }  // namespace pbit

@@ -164,6 +164,7 @@ struct SparseVariant {
     bool unit = false;
     bool table = false;
     int warp_g = 0;      // trials per thread of the warp-table tile (0: not used); see pbit_tile.cuh
+    bool warp_half = false;  // the warp-table tile indexes its lanes by count / 2 (HALF)
 };
 SparseVariant choose_sparse_variant(const Graph& g, int32_t T);
 // Trials per thread of the warp-table tile (32, 16, or 0: not applicable); `wide` for many

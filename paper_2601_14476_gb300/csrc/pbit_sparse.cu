@@ -76,10 +76,10 @@ __global__ void __launch_bounds__(kBlock) sparse_step_kernel(StepArgs a) {
 
 // Warp-table tile; six resident blocks per SM (40 registers): on the torus at T = 1024 this ran
 // 33.5 µs per step, against 33.7 (five), 35.5 (four) and 36.2 (seven or eight, with spills).
-template <int G>
+template <int G, bool HALF>
 __global__ void __launch_bounds__(kBlock, 6) sparse_warp_kernel(StepArgs a) {
     step_dependency();
-    process_tile_warp<G>(a, blockIdx.x * (uint32_t)kBlock);
+    process_tile_warp<G, HALF>(a, blockIdx.x * (uint32_t)kBlock);
 }
 
 // A step launch with programmatic stream serialization, or a plain one when PBIT_NO_PDL is set or the
@@ -131,13 +131,13 @@ cudaError_t launch_step_g(const StepArgs& base, cudaStream_t s) {
     return e;
 }
 
-template <int G>
+template <int G, bool HALF>
 cudaError_t launch_warp_g(const StepArgs& base, cudaStream_t s) {
     StepArgs a = base;
     set_group_divisor(a, G);
     const int64_t threads = (int64_t)a.n * (a.T / G);
     const int64_t blocks = (threads + kBlock - 1) / kBlock;
-    const cudaError_t e = launch_step_pdl(sparse_warp_kernel<G>, (unsigned)blocks, a, s);
+    const cudaError_t e = launch_step_pdl(sparse_warp_kernel<G, HALF>, (unsigned)blocks, a, s);
     count_launches(1);
     return e;
 }
@@ -393,6 +393,8 @@ SparseVariant choose_sparse_variant(const Graph& g, int32_t T) {
     if (plain) return v;
     static const bool no_warp = std::getenv("PBIT_SPARSE_NOWARP") != nullptr;  // force the block-table tile
     v.warp_g = no_warp ? 0 : warp_tile_group(g, T, false);
+    // the warp tile indexes its lanes by count / 2 only where 2 deg + 1 lanes do not fit
+    v.warp_half = v.warp_g != 0 && 2 * (int64_t)g.max_degree + 1 > std::min<int64_t>(32, T / v.warp_g);
     const int G = T % 16 == 0 ? 16 : (T % 4 == 0 ? 4 : 1);
     v.unit = g.unit_weights && g.max_degree <= 127 && G >= 4;
     // table when its entries stay within shared memory and cost well under one per update
@@ -412,8 +414,8 @@ cudaError_t launch_sparse_step(const StepArgs& a, cudaStream_t s, SparseVariant 
         return launch_variant_g<1, false>(a, s);
     }
     if (v.warp_g != 0 && G == 16) {  // G == 16: T % 16 == 0 and both buffers 16-byte aligned
-        if (v.warp_g == 32) return launch_warp_g<32>(a, s);
-        return launch_warp_g<16>(a, s);
+        if (v.warp_g == 32) return v.warp_half ? launch_warp_g<32, true>(a, s) : launch_warp_g<32, false>(a, s);
+        return v.warp_half ? launch_warp_g<16, true>(a, s) : launch_warp_g<16, false>(a, s);
     }
     if (G == 16) return launch_step_variant<16>(a, s, v);
     if (G == 4) return launch_step_variant<4>(a, s, v);

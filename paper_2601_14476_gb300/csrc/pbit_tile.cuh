@@ -270,12 +270,14 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
 // node lives in registers of the warp lanes that update it.  A warp covers
 // either part of one node's trials (T / G >= 32 groups per node) or several
 // whole nodes (T / G divides 32), so each node owns a segment of L lanes,
-// L = min(32, T / G).  Lane seg + c holds the negated threshold for the field
+// L = min(32, T / G).  The update with packed count c2 = 2 * #(J_ij s_j = -1)
+// (field h_i + deg_i - c2) reads its threshold with one shuffle from its
+// segment.  HALF: lane seg + c holds the negated threshold for the field
 // h_i + deg_i - 2c (c = 0..deg_i, needing deg_i + 1 <= L: the field of a node
-// with unit weights has the parity of its degree), and the update with
-// packed count c2 = 2 * #(J_ij s_j = -1) reads it with one shuffle from lane
-// seg + c2 / 2 (the field is h_i + deg_i - c2).  No shared memory, no block
-// barrier.
+// with unit weights has the parity of its degree) and the lookup index is
+// c2 / 2; otherwise lane seg + c holds the field h_i + deg_i - c (needing
+// 2 deg_i + 1 <= L) and the index is c2 itself, which saves the halving.
+// No shared memory, no block barrier.
 //
 // Decisions without branches or multiplies: (w >> 8) - kthr is negative
 // exactly when the p-bit draw picks +1 (both sides below 2^25), and
@@ -283,7 +285,7 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
 // turned into byte masks with prmt's sign-replicating selectors, and
 //   new = U ? (S ? 0x01 : 0xFF) : old = ((U & ~S) | (~U & old)) | 0x01
 // per byte (every spin byte is 0x01 or 0xFF, so bit 0 is always set).
-template <int G>
+template <int G, bool HALF>
 __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t tid) {
     static_assert(G == 16 || G == 32, "warp-table tile needs 4-word trial groups");
     constexpr int NW = Pack<G>::W;
@@ -303,7 +305,7 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     const uint32_t thr = a.par.thr ? __ldg(a.par.thr + i) : (1u << 24);
     const int rb = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
     const int deg = re - rb;
-    const uint32_t negk_lane = 0u - pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + deg - 2 * ell));
+    const uint32_t negk_lane = 0u - pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + deg - (HALF ? 2 * ell : ell)));
     uint32_t cnt2[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) cnt2[w] = 0;
@@ -334,7 +336,7 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
         uint4 r[2];
         r[0] = philox_tail(ph, (uint32_t)(t0 + 4 * w) >> 1, a.seed_lo, a.seed_hi);
         r[1] = philox_tail(ph, (uint32_t)(t0 + 4 * w + 2) >> 1, a.seed_lo, a.seed_hi);
-        const uint32_t cnt = cnt2[w] >> 1;  // every byte of cnt2 is even: halving keeps the bytes apart
+        const uint32_t cnt = HALF ? cnt2[w] >> 1 : cnt2[w];  // bytes of cnt2 are even: halving keeps them apart
         uint32_t dr[4], du[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -353,9 +355,9 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     if (live) store_group<G>(a.out + (size_t)i * a.T + t0, neww);
 }
 
-template <int G>
+template <int G, bool HALF>
 __device__ __forceinline__ void process_tile_warp(const StepArgs& a, uint32_t first) {
-    process_warp_items<G>(a, first + threadIdx.x);  // first is a multiple of the block size
+    process_warp_items<G, HALF>(a, first + threadIdx.x);  // first is a multiple of the block size
 }
 
 // The pSA variants of the Methods section (Eq. SpSA, Eq. TApSA) and the
