@@ -41,22 +41,22 @@ TRAFFIC = {
     # one persistent launch: K_2000 +-1, 256 trials, 2000 steps, e4m3 kernel (weights outside e2m1)
     "dense_persistent_kernel": {"bytes": None, "files": ["pbit_dense.cu", "pbit_device.cuh"], "sha": None},
     # one cluster-resident FP4 launch: K_2000 +-1, 256 trials, 2000 steps
-    "dense4_cluster_kernel": {"bytes": 3063040 + 0, "files": ["pbit_dense4.cu", "pbit_device.cuh"],
-                              "sha": "c819315bf97055f4"},
+    "dense4_cluster_kernel": {"bytes": 2989312 + 0, "files": ["pbit_dense4.cu", "pbit_device.cuh"],
+                              "sha": "9531f8b17a5f31c5"},
     # one multi-step launch: 100x200 torus, 1024 trials, 5000 steps
-    "sparse_flow_kernel": {"bytes": 23571712 + 70528768,
+    "sparse_flow_kernel": {"bytes": 23502592 + 69804288,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
-                           "sha": "3da07a51abfda9e2"},
+                           "sha": "c116ca22e431f323"},
     # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
-    "sparse_variant_words_kernel:spsa": {"bytes": 103565738 + 41299968,
+    "sparse_variant_words_kernel:spsa": {"bytes": 103563178 + 41197141,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "12f4d2bba397f137"},
-    "sparse_variant_words_kernel:tapsa": {"bytes": 144543061 + 35486720,
+                                         "sha": "151f58073eddfe83"},
+    "sparse_variant_words_kernel:tapsa": {"bytes": 144534613 + 35485696,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "12f4d2bba397f137"},
+                                          "sha": "151f58073eddfe83"},
     # per launch of a 64-step chunk of all 64 instances of the uneven batch
-    "batch_chunk_kernel": {"bytes": 633134848 + 1197323008, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
-                           "sha": "662a07b8d751b150", "chunk_steps": 64},
+    "batch_chunk_kernel": {"bytes": 1354917888 + 2004216064, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
+                           "sha": "9249f5b4ba245cc7", "chunk_steps": 64},
 }
 
 
