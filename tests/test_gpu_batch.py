@@ -110,3 +110,37 @@ def test_batch64_smallest_instances_match_oracle():
         got = B.cuts(k)
         assert (got == ref_cut).mean() >= 0.75, (k, got, ref_cut)
         assert abs(got.mean() - ref_cut.mean()) <= 0.005 * abs(ref_cut.mean())
+
+
+def _heavy_mix():
+    """Twenty instances holding at least four tiles per resident CTA and step: the chunk plan then
+    takes the warp-table tile with 32 trials per thread for the 100x100 tori at T = 256 and two-tile
+    work items, and the shared-table tile for G(n, 3n) at T = 128 (degrees too high for the warp tile)."""
+    gs, kws = [], []
+    for k in range(20):
+        if k % 5 == 4:
+            g, T = inputs.erdos_renyi_gnm(4000, 12000, 50 + k, "+1"), 128
+        else:
+            g, T = inputs.torus_2d(100, 100, 50 + k, "pm1"), 256
+        var = inputs.variability(g.n, k) if k % 2 else None
+        gs.append(g)
+        kws.append(dict(trials=T, steps=20 + k, seed=300 + k, instance=k, variability=var))
+    # the heavy condition with the plain kernel's occupancy (8 blocks of 256 threads per SM)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tiles = sum(-(-g.n * (kw["trials"] // (32 if kw["trials"] == 256 else 16)) // 256) for g, kw in zip(gs, kws))
+    assert len(gs) >= 16 and tiles >= 4 * sms * 8
+    return gs, kws
+
+
+def test_heavy_plan_equals_alone():
+    """The heavy-load tiling (warp-table tile at 32 trials per thread, two tiles per item) gives every
+    instance exactly its own pbit_anneal result."""
+    gs, kws = _heavy_mix()
+    Gs = [pbit.Graph.from_inputs(g) for g in gs]
+    B = pbit.Batch(Gs, kws)
+    B.run(chunk_steps=16)
+    torch.cuda.synchronize()
+    for k, (G, kw) in enumerate(zip(Gs, kws)):
+        assert B.progress(k) == kw["steps"]
+        assert np.array_equal(B.spins(k).cpu().numpy(), _alone(G, kw)), k
+    Gs[0].status()

@@ -119,3 +119,37 @@ def test_served_request_matches_oracle_in_the_mix():
                                   instance=target.instance, var=target.var))
     assert (got == ref).mean() >= 0.75, (got, ref)
     assert abs(got.mean() - ref.mean()) <= 0.005 * ref.mean()
+
+
+def test_server_heavy_load_results_equal_alone():
+    """Twenty large requests resident at once: the server plans its chunks for a heavy load
+    (warp-table tile at 32 trials per thread, two-tile items) and every result equals the same
+    anneal run alone."""
+    gs, Ts = [], []
+    for k in range(20):
+        if k % 5 == 4:
+            gs.append(inputs.erdos_renyi_gnm(4000, 12000, 70 + k, "+1"))
+            Ts.append(128)
+        else:
+            gs.append(inputs.torus_2d(100, 100, 70 + k, "pm1"))
+            Ts.append(256)
+    Gs = [pbit.Graph.from_inputs(g) for g in gs]
+    srv = pbit.pbit_server_create(16 << 30, 32, 16)
+    try:
+        keep, ids, kws = [], [], []
+        for k, (G, g, T) in enumerate(zip(Gs, gs, Ts)):
+            kw = dict(trials=T, steps=160 + k, seed=500 + k, instance=k,
+                      variability=inputs.variability(g.n, k) if k % 2 else None)
+            p, kp = pbit.make_params(**kw)
+            keep.append((p, kp))
+            kws.append(kw)
+            ids.append(pbit.pbit_server_submit(srv, G.handle, p))
+        for rid, G, kw in zip(ids, Gs, kws):
+            code, cuts, lat = pbit.pbit_server_wait(srv, rid, kw["trials"], timeout_s=120)
+            assert code == pbit.PBIT_OK
+            alone = G.anneal(kw["trials"], kw["steps"], seed=kw["seed"], instance=kw["instance"],
+                             variability=kw["variability"], kernel=pbit.KERNEL_SPARSE)
+            assert np.array_equal(cuts, G.cut(alone))
+        assert pbit.pbit_server_stats(srv)["peak_resident"] >= 16
+    finally:
+        pbit.pbit_server_destroy(srv)
