@@ -205,8 +205,11 @@ void pbit_anneal_params_default(pbit_anneal_params* p);
  * allocates its scratch with cudaMallocAsync on that stream and copies the
  * per-node parameters from host memory, so it is not for use under stream
  * capture.  Scratch: up to three n*T spin buffers, the variant state
- * when p->state is NULL, and under the timing model 8n + 2m bytes of periods,
- * node order and period buckets.  Errors: PBIT_E_INVALID, PBIT_E_UNSUPPORTED
+ * when p->state is NULL, under the timing model 8n + 2m bytes of periods,
+ * node order and period buckets, and for the packed-FP4 dense kernel
+ * 1.5 * K * T' bytes (K = n rounded up to 128, T' = T rounded up to the
+ * kernel's trial group of 32 or 48): the packed start spins and the staging
+ * slots through which each step's spin slices are exchanged.  Errors: PBIT_E_INVALID, PBIT_E_UNSUPPORTED
  * (forced kernel cannot run the shape; TApSA fields beyond int16),
  * PBIT_E_NOMEM, PBIT_E_CUDA.
  */
