@@ -114,12 +114,18 @@ def test_batch64_smallest_instances_match_oracle():
 
 def _heavy_mix():
     """Twenty instances holding at least four tiles per resident CTA and step: the chunk plan then
-    takes the warp-table tile with 32 trials per thread for the 100x100 tori at T = 256 and two-tile
-    work items, and the shared-table tile for G(n, 3n) at T = 128 (degrees too high for the warp tile)."""
+    takes the warp-table tile with 32 trials per thread for the 100x100 tori at T = 256, with 16 for
+    3-NN graphs of maximum degree 8-15 at T = 256 (deg + 1 counts exceed the 8 lanes a node has at
+    32), two-tile work items, and the shared-table tile for G(n, 3n) at T = 128 (degrees too high
+    for the warp tile)."""
     gs, kws = [], []
     for k in range(20):
         if k % 5 == 4:
             g, T = inputs.erdos_renyi_gnm(4000, 12000, 50 + k, "+1"), 128
+        elif k % 5 == 3:
+            g, T = inputs.rgg_knn(10000, 50 + k, 3, "pm1"), 256
+            deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).max()
+            assert 8 <= deg <= 15, deg  # the warp-table tile at 16 trials per thread
         else:
             g, T = inputs.torus_2d(100, 100, 50 + k, "pm1"), 256
         var = inputs.variability(g.n, k) if k % 2 else None

@@ -123,13 +123,16 @@ def test_served_request_matches_oracle_in_the_mix():
 
 def test_server_heavy_load_results_equal_alone():
     """Twenty large requests resident at once: the server plans its chunks for a heavy load
-    (warp-table tile at 32 trials per thread, two-tile items) and every result equals the same
-    anneal run alone."""
+    (warp-table tile at 32 or 16 trials per thread, two-tile items)
+    and every result equals the same anneal run alone."""
     gs, Ts = [], []
     for k in range(20):
         if k % 5 == 4:
             gs.append(inputs.erdos_renyi_gnm(4000, 12000, 70 + k, "+1"))
             Ts.append(128)
+        elif k % 5 == 3:  # maximum degree 8 or more: the warp-table tile at 16 trials per thread
+            gs.append(inputs.rgg_knn(10000, 70 + k, 3, "pm1"))
+            Ts.append(256)
         else:
             gs.append(inputs.torus_2d(100, 100, 70 + k, "pm1"))
             Ts.append(256)
