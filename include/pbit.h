@@ -23,9 +23,12 @@
  *    stream.  Work is enqueued on it in order; entry points that return
  *    results in host memory synchronise that stream before returning.
  *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key =
- *    (seed low word, seed high word) and counter = (node, step, instance,
- *    trial/2); the even trial of a pair uses output words (0,1), the odd one
- *    (2,3), as (r, u): r = (2*(w0>>8)+1-2^24)/2^24, u = (w1>>8)/2^24.  The
+ *    (seed low word, seed high word) and counter = (node, step, instance, c).
+ *    The trials 8g .. 8g+7 share the blocks c = 3g, 3g+1, 3g+2 (all 384 bits
+ *    used).  Trial k = t mod 8 takes output word k mod 4 of block 3g + k/4 as
+ *    its r-word wr: r = (2*(wr>>8)+1-2^24)/2^24; its u = q/2^24 with the
+ *    24-bit q = (half (k mod 2) of output word k/2 of block 3g+2) * 2^8 +
+ *    (wr & 0xFF).  The
  *    initial state (step counter 0xFFFFFFFF) is +1 iff r < 0.  Results are
  *    therefore a pure function of (graph, parameters, seed, instance) and do
  *    not depend on the kernel, batch or server slot that computed them.

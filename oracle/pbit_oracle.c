@@ -37,8 +37,12 @@
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), written here from that paper's
- * definition.  key = (seed_lo, seed_hi); counter = (node, step, instance,
- * trial/2); trial parity selects output words (0,1) or (2,3) as (r, u).
+ * definition.  key = (seed_lo, seed_hi); counter = (node, step, instance, c).
+ * The eight trials 8g .. 8g+7 of a (node, step, instance) share the three
+ * blocks c = 3g, 3g+1, 3g+2 (384 bits, 48 per trial).  Trial k = trial mod 8:
+ * r-word = output word (k mod 4) of block 3g + k/4, r index = its top 24 bits;
+ * u index (24 bits) = the 16 bits of half (k mod 2) of output word k/2 of block
+ * 3g+2 (the high part), then the r-word's low 8 bits.
  * The initial state uses step = 0xFFFFFFFF and sets +1 iff r < 0.
  *
  * Pins (tests/test_oracle_pins.py): brute-force MAX-CUT for n <= 20, the
@@ -94,12 +98,17 @@ typedef struct {
 } orc_draw;
 
 static orc_draw orc_draw_for(uint64_t seed, uint32_t instance, int32_t node, uint32_t step, int32_t trial) {
-    uint32_t ctr[4] = {(uint32_t)node, step, instance, (uint32_t)trial >> 1};
+    uint32_t group = (uint32_t)trial / 8u, kk = (uint32_t)trial % 8u;
     uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
-    uint32_t w[4];
-    orc_philox4x32_10(ctr, key, w);
-    uint32_t wr = w[2 * (trial & 1)], wu = w[2 * (trial & 1) + 1];
-    uint32_t k = wr >> 8, q = wu >> 8;
+    uint32_t ctr_r[4] = {(uint32_t)node, step, instance, 3u * group + kk / 4u};
+    uint32_t ctr_u[4] = {(uint32_t)node, step, instance, 3u * group + 2u};
+    uint32_t wr_block[4], wu_block[4];
+    orc_philox4x32_10(ctr_r, key, wr_block);
+    orc_philox4x32_10(ctr_u, key, wu_block);
+    uint32_t wr = wr_block[kk % 4u];
+    uint32_t u_high = (wu_block[kk / 2u] >> (16u * (kk % 2u))) & 0xFFFFu;
+    uint32_t k = wr >> 8;                    /* top 24 bits of the r-word */
+    uint32_t q = (u_high << 8) | (wr & 0xFFu); /* 16 + 8 bits */
     orc_draw d;
     d.r = ((double)(2.0 * (double)k + 1.0) - 16777216.0) / 16777216.0;
     d.u = (double)q / 16777216.0;

@@ -354,8 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) dense_step_kernel(DenseArgs a) {
         for (int q = 0; q < 16; q += 2) {
             if (q < cnt) {
                 const int t = tb * NT + c + q;  // even
-                const uint4 rw =
-                    philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t >> 1, a.seed_lo, a.seed_hi);
+                const uint4 rw = pbit_draws2((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t, a.seed_lo, a.seed_hi);
                 const int D0 = hi + __float2int_rn(acc[q]);
                 const int D1 = hi + __float2int_rn(acc[q + 1]);
                 const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, D0));
@@ -542,8 +541,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
             const int i0 = rb * kRows + (tid & 31) * 4;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                s_rw[k * kEpi + tid] = philox((uint32_t)(i0 + k), (uint32_t)step, a.instance, (uint32_t)t0 >> 1,
-                                              a.seed_lo, a.seed_hi);
+                s_rw[k * kEpi + tid] = pbit_draws2((uint32_t)(i0 + k), (uint32_t)step, a.instance, (uint32_t)t0,
+                                                   a.seed_lo, a.seed_hi);
             if (ls == 0) {
 #pragma unroll
                 for (int slot = 0; slot < kMaxItems; ++slot) {
@@ -619,8 +618,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                         if (i < a.n) {
                             const int r = r0 + k;
                             const uint4 rw = slot == 0 ? s_rw[k * kEpi + tid]
-                                                       : philox((uint32_t)i, (uint32_t)step, a.instance,
-                                                                (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
+                                                       : pbit_draws2((uint32_t)i, (uint32_t)step, a.instance,
+                                                                     (uint32_t)t0, a.seed_lo, a.seed_hi);
                             const float lam = s_lam[r], del = s_del[r];
                             const uint32_t thr = s_thr[r];
                             const int D0 = s_h[r] + f0[k];

@@ -210,6 +210,17 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// The Philox words of one row's 16 trials t0 .. t0 + 15 (two groups of 8, t0 a
+// multiple of 16): rw[j / 2] holds trials t0 + 2 (j / 2) and the next as (r0, u0, r1, u1).
+__device__ __forceinline__ void draw16(const PhiloxHead& ph, uint32_t t0, uint32_t k0, uint32_t k1, uint4 (&rw)[8]) {
+#pragma unroll
+    for (int gq = 0; gq < 2; ++gq) {
+        const PbitPairs8 d = pbit_pairs8(ph, t0 + 8u * gq, k0, k1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rw[4 * gq + q] = d.p[q];
+    }
+}
+
 // The p-bit input x of pbit_input for a field already held as an exact float (|D| < 2^24, so the
 // value equals pbit_input's for the same integer field).
 __device__ __forceinline__ float pbit_input_f(int mode, float I0, float lam, float del, float d) {
@@ -376,9 +387,7 @@ __global__ void __launch_bounds__((N / 4 + 2) * 32, 1) dense4_cluster_kernel(D4A
         if (L > 0) {
             I0 = a.i0_table[a.step_begin];
             const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step_begin, a.instance, a.seed_lo, a.seed_hi);
-#pragma unroll
-            for (int j2 = 0; j2 < 8; ++j2)
-                rw[j2] = philox_tail(ph, (uint32_t)(t0 + 2 * j2) >> 1, a.seed_lo, a.seed_hi);
+            draw16(ph, (uint32_t)t0, a.seed_lo, a.seed_hi, rw);
         }
     }
     const uint32_t idesc = idesc_mxf4((uint32_t)N);
@@ -513,8 +522,7 @@ __global__ void __launch_bounds__((N / 4 + 2) * 32, 1) dense4_cluster_kernel(D4A
         // I0 and the Philox words of the next step, drawn while the copies and the next MMAs run
         I0 = a.i0_table[step + 1];
         const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)(step + 1), a.instance, a.seed_lo, a.seed_hi);
-#pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) rw[j2] = philox_tail(ph, (uint32_t)(t0 + 2 * j2) >> 1, a.seed_lo, a.seed_hi);
+        draw16(ph, (uint32_t)t0, a.seed_lo, a.seed_hi, rw);
     }
     // final state of this thread's row and trials (left untouched when a wait gave up: the result of
     // that call is undefined and PBIT_E_TIMEOUT reports it)

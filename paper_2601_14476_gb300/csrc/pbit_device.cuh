@@ -125,6 +125,87 @@ __device__ __forceinline__ uint4 philox_tail(const PhiloxHead& h, uint32_t c3, u
     return make_uint4(x0, x1, x2, x3);
 }
 
+// The random draws of one (node, step, instance) for its trials (the r of
+// Eq. 6 and the timing draw u, both on 2^24-point grids).  Trials 8g .. 8g+7
+// share three Philox blocks, B0, B1, B2, at last counter words 3g, 3g+1 and
+// 3g+2, and all 384 of their bits are used: trial k of the group (k = t mod 8)
+// takes word k mod 4 of block k / 4 as its r-word (r from the top 24 bits);
+// its 24-bit u has half (k mod 2) of word k / 2 of B2 as its high 16 bits and
+// the r-word's low byte as its low 8.  pbit_uword returns u in bits 8..31 of
+// a word (bits 0..7 repeat the r-word's low byte), so that callers compare
+// (word >> 8) for r and u alike.
+__device__ __forceinline__ uint32_t pbit_uword(uint32_t wr, uint32_t w2, bool odd) {
+    return __byte_perm(wr, w2, odd ? 0x7600u : 0x5400u);
+}
+
+__device__ __forceinline__ uint32_t pbit_word(const uint4& b, int c) {
+    return c == 0 ? b.x : (c == 1 ? b.y : (c == 2 ? b.z : b.w));
+}
+
+// r- and u-words of the four trials t .. t+3 (t a multiple of 4): the block of
+// their r-words (3g + h, h the half of the group) and B2.
+__device__ __forceinline__ void pbit_draws4(uint32_t i, uint32_t step, uint32_t instance, uint32_t t, uint32_t k0,
+                                            uint32_t k1, uint32_t (&wr)[4], uint32_t (&wu)[4]) {
+    const uint32_t g3 = 3u * (t >> 3), h = (t >> 2) & 1u;
+    uint4 a, b2;
+    philox_pair(i, step, instance, g3 + h, g3 + 2u, k0, k1, a, b2);
+    const uint32_t s0 = h ? b2.z : b2.x, s1 = h ? b2.w : b2.y;
+    wr[0] = a.x;
+    wr[1] = a.y;
+    wr[2] = a.z;
+    wr[3] = a.w;
+    wu[0] = pbit_uword(a.x, s0, false);
+    wu[1] = pbit_uword(a.y, s0, true);
+    wu[2] = pbit_uword(a.z, s1, false);
+    wu[3] = pbit_uword(a.w, s1, true);
+}
+
+// The same for the two trials t, t+1 (t even), as (r0, u0, r1, u1).
+__device__ __forceinline__ uint4 pbit_draws2(uint32_t i, uint32_t step, uint32_t instance, uint32_t t, uint32_t k0,
+                                             uint32_t k1) {
+    const uint32_t g3 = 3u * (t >> 3), k = t & 7u;
+    uint4 a, b2;
+    philox_pair(i, step, instance, g3 + (k >> 2), g3 + 2u, k0, k1, a, b2);
+    const uint32_t r0 = (k & 2u) ? a.z : a.x, r1 = (k & 2u) ? a.w : a.y;
+    const uint32_t s = pbit_word(b2, (int)(k >> 1));
+    return make_uint4(r0, pbit_uword(r0, s, false), r1, pbit_uword(r1, s, true));
+}
+
+// The same for one trial t.
+__device__ __forceinline__ void pbit_draw1(uint32_t i, uint32_t step, uint32_t instance, uint32_t t, uint32_t k0,
+                                           uint32_t k1, uint32_t& wr, uint32_t& wu) {
+    const uint4 d = pbit_draws2(i, step, instance, t & ~1u, k0, k1);
+    wr = (t & 1u) ? d.z : d.x;
+    wu = (t & 1u) ? d.w : d.y;
+}
+
+// The r-word alone of trial t (the initial state needs only r).
+__device__ __forceinline__ uint32_t pbit_rword(uint32_t i, uint32_t step, uint32_t instance, uint32_t t, uint32_t k0,
+                                               uint32_t k1) {
+    const uint4 b = philox(i, step, instance, 3u * (t >> 3) + ((t >> 2) & 1u), k0, k1);
+    return pbit_word(b, (int)(t & 3u));
+}
+
+// The four trial pairs of the group starting at trial t (a multiple of 8) from
+// the head of their (node, step, instance): pair q holds trials t + 2q and
+// t + 2q + 1 as (r0, u0, r1, u1).
+struct PbitPairs8 {
+    uint4 p[4];
+};
+
+__device__ __forceinline__ PbitPairs8 pbit_pairs8(const PhiloxHead& h, uint32_t t, uint32_t k0, uint32_t k1) {
+    const uint32_t g3 = 3u * (t >> 3);
+    const uint4 b2 = philox_tail(h, g3 + 2u, k0, k1);
+    const uint4 b0 = philox_tail(h, g3, k0, k1);
+    const uint4 b1 = philox_tail(h, g3 + 1u, k0, k1);
+    PbitPairs8 r;
+    r.p[0] = make_uint4(b0.x, pbit_uword(b0.x, b2.x, false), b0.y, pbit_uword(b0.y, b2.x, true));
+    r.p[1] = make_uint4(b0.z, pbit_uword(b0.z, b2.y, false), b0.w, pbit_uword(b0.w, b2.y, true));
+    r.p[2] = make_uint4(b1.x, pbit_uword(b1.x, b2.z, false), b1.y, pbit_uword(b1.y, b2.z, true));
+    r.p[3] = make_uint4(b1.z, pbit_uword(b1.z, b2.w, false), b1.w, pbit_uword(b1.w, b2.w, true));
+    return r;
+}
+
 // The p-bit input x for an exact integer field D (three placements of the
 // offset; see pbit_offset_mode).  Every operation is an explicitly rounded
 // float32 operation, so the value does not depend on compiler contraction.

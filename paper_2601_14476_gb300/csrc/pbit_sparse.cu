@@ -32,8 +32,7 @@ __global__ void init_spins_kernel(int32_t n, int32_t T, uint32_t k0, uint32_t k1
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx / T), t = (int)(idx - (int64_t)i * T);
-        const uint4 r = philox((uint32_t)i, 0xFFFFFFFFu, instance, (uint32_t)t >> 1, k0, k1);
-        const uint32_t wr = (t & 1) ? r.z : r.x;
+        const uint32_t wr = pbit_rword((uint32_t)i, 0xFFFFFFFFu, instance, (uint32_t)t, k0, k1);
         spins[idx] = ((wr >> 8) < (1u << 23)) ? 1 : -1;  // +1 iff r < 0
     }
 }

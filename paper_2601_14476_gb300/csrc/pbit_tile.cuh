@@ -90,24 +90,24 @@ __device__ __forceinline__ void decide_group(const StepArgs& a, int i, int t0, c
     const int hi = a.h ? __ldg(a.h + i) : 0;
 #pragma unroll
     for (int k = 0; k < Pack<G>::W; ++k) neww[k] = 0;
+    static_assert(G == 1 || G % 4 == 0, "trial groups of 1 or a multiple of 4");
     if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
-        const bool odd = t0 & 1;
-        const uint32_t wr = odd ? r.z : r.x, wu = odd ? r.w : r.y;
+        uint32_t wr, wu;
+        pbit_draw1((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0, a.seed_lo, a.seed_hi, wr, wu);
         const uint32_t kthr = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[0]));
         const int s = pbit_next(wr, wu, kthr, thr, sbyte(oldw[0], 0));
         neww[0] = (uint32_t)(uint8_t)(int8_t)s;
     } else {
 #pragma unroll
-        for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)(t0 + k) >> 1, a.seed_lo,
-                                   a.seed_hi);
-            const uint32_t k0 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k]));
-            const uint32_t k1 = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k + 1]));
-            const int s0 = pbit_next(r.x, r.y, k0, thr, sbyte(oldw[k >> 2], k & 3));
-            const int s1 = pbit_next(r.z, r.w, k1, thr, sbyte(oldw[k >> 2], (k & 3) + 1));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
+        for (int k = 0; k < G; k += 4) {
+            uint32_t wr[4], wu[4];
+            pbit_draws4((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)(t0 + k), a.seed_lo, a.seed_hi, wr, wu);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t kt = pbit_kthr_of_x(pbit_input(a.offset_mode, I0, lam, del, hi + acc[k + b]));
+                const int s = pbit_next(wr[b], wu[b], kt, thr, sbyte(oldw[k >> 2], b));
+                neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s) << (8 * b);
+            }
         }
     }
 }
@@ -235,29 +235,40 @@ __device__ __forceinline__ void process_tile(const StepArgs& a, int64_t first, u
     uint32_t oldw[NW], neww[NW];
     load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
     if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
-        const bool odd = t0 & 1;
-        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr_at(0), thr, sbyte(oldw[0], 0));
+        uint32_t wr, wu;
+        pbit_draw1((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0, a.seed_lo, a.seed_hi, wr, wu);
+        const int s = pbit_next(wr, wu, kthr_at(0), thr, sbyte(oldw[0], 0));
         neww[0] = (uint32_t)(uint8_t)(int8_t)s;
     } else {
         // sign tests and byte masks as in the warp-table tile
-        const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step, a.instance, a.seed_lo, a.seed_hi);
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            uint4 r[2];
-            r[0] = philox_tail(ph, (uint32_t)(t0 + 4 * w) >> 1, a.seed_lo, a.seed_hi);
-            r[1] = philox_tail(ph, (uint32_t)(t0 + 4 * w + 2) >> 1, a.seed_lo, a.seed_hi);
+        const auto decide_word = [&](int w, const uint32_t (&wr)[4], const uint32_t (&wu)[4]) {
             uint32_t dr[4], du[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                dr[2 * h] = (r[h].x >> 8) - kthr_at(4 * w + 2 * h);
-                du[2 * h] = (r[h].y >> 8) - thr;
-                dr[2 * h + 1] = (r[h].z >> 8) - kthr_at(4 * w + 2 * h + 1);
-                du[2 * h + 1] = (r[h].w >> 8) - thr;
+            for (int b = 0; b < 4; ++b) {
+                dr[b] = (wr[b] >> 8) - kthr_at(4 * w + b);
+                du[b] = (wu[b] >> 8) - thr;
             }
             const uint32_t S = sign_bytes(dr[0], dr[1], dr[2], dr[3]);
             const uint32_t U = sign_bytes(du[0], du[1], du[2], du[3]);
             neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
+        };
+        if constexpr (G == 4) {
+            uint32_t wr[4], wu[4];
+            pbit_draws4((uint32_t)i, (uint32_t)a.step, a.instance, (uint32_t)t0, a.seed_lo, a.seed_hi, wr, wu);
+            decide_word(0, wr, wu);
+        } else {
+            // whole groups of 8 trials: three Philox blocks per group
+            const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step, a.instance, a.seed_lo, a.seed_hi);
+#pragma unroll
+            for (int gq = 0; gq < NW / 2; ++gq) {
+                const PbitPairs8 d = pbit_pairs8(ph, (uint32_t)(t0 + 8 * gq), a.seed_lo, a.seed_hi);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint4 p0 = d.p[2 * h], p1 = d.p[2 * h + 1];
+                    const uint32_t wr[4] = {p0.x, p0.z, p1.x, p1.z}, wu[4] = {p0.y, p0.w, p1.y, p1.w};
+                    decide_word(2 * gq + h, wr, wu);
+                }
+            }
         }
     }
     store_group<G>(a.out + (size_t)i * a.T + t0, neww);
@@ -332,25 +343,26 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     load_group<G>(a.in + (size_t)i * a.T + t0, oldw);
     const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step, a.instance, a.seed_lo, a.seed_hi);
 #pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        uint4 r[2];
-        r[0] = philox_tail(ph, (uint32_t)(t0 + 4 * w) >> 1, a.seed_lo, a.seed_hi);
-        r[1] = philox_tail(ph, (uint32_t)(t0 + 4 * w + 2) >> 1, a.seed_lo, a.seed_hi);
-        const uint32_t cnt = HALF ? cnt2[w] >> 1 : cnt2[w];  // bytes of cnt2 are even: halving keeps them apart
-        uint32_t dr[4], du[4];
+    for (int gq = 0; gq < NW / 2; ++gq) {
+        // one group of 8 trials (two words) from three Philox blocks: the u-halves of both words
+        // first, then each word's r-block
+        const uint32_t g3 = 3u * ((uint32_t)(t0 + 8 * gq) >> 3);
+        const uint4 b2 = philox_tail(ph, g3 + 2u, a.seed_lo, a.seed_hi);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
+            const int w = 2 * gq + h;
+            const uint4 r = philox_tail(ph, g3 + (uint32_t)h, a.seed_lo, a.seed_hi);
+            const uint32_t s0 = h ? b2.z : b2.x, s1 = h ? b2.w : b2.y;
+            const uint32_t cnt = HALF ? cnt2[w] >> 1 : cnt2[w];  // bytes of cnt2 are even: halving keeps them apart
             // the shuffle width L keeps the source lane inside this node's segment
-            const uint32_t q0 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt, 2 * h), L);
-            const uint32_t q1 = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt, 2 * h + 1), L);
-            dr[2 * h] = (r[h].x >> 8) + q0;
-            du[2 * h] = (r[h].y >> 8) - thr;
-            dr[2 * h + 1] = (r[h].z >> 8) + q1;
-            du[2 * h + 1] = (r[h].w >> 8) - thr;
+            uint32_t q[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) q[b] = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt, b), L);
+            const uint32_t S = sign_bytes((r.x >> 8) + q[0], (r.y >> 8) + q[1], (r.z >> 8) + q[2], (r.w >> 8) + q[3]);
+            const uint32_t U = sign_bytes((pbit_uword(r.x, s0, false) >> 8) - thr, (pbit_uword(r.y, s0, true) >> 8) - thr,
+                                          (pbit_uword(r.z, s1, false) >> 8) - thr, (pbit_uword(r.w, s1, true) >> 8) - thr);
+            neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
         }
-        const uint32_t S = sign_bytes(dr[0], dr[1], dr[2], dr[3]);
-        const uint32_t U = sign_bytes(du[0], du[1], du[2], du[3]);
-        neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
     }
     if (live) store_group<G>(a.out + (size_t)i * a.T + t0, neww);
 }
@@ -451,22 +463,24 @@ __device__ __forceinline__ void process_tile_variant(const StepArgs& a, int64_t 
     uint32_t neww[Pack<G>::W];
 #pragma unroll
     for (int w = 0; w < Pack<G>::W; ++w) neww[w] = 0;
+    static_assert(G == 1 || G % 4 == 0, "trial groups of 1 or a multiple of 4");
     if constexpr (G == 1) {
-        const uint4 r = philox((uint32_t)i, q, a.instance, (uint32_t)t0 >> 1, a.seed_lo, a.seed_hi);
-        const bool odd = t0 & 1;
+        uint32_t wr, wu;
+        pbit_draw1((uint32_t)i, q, a.instance, (uint32_t)t0, a.seed_lo, a.seed_hi, wr, wu);
         const uint32_t kthr = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[0]));
-        const int s = pbit_next(odd ? r.z : r.x, odd ? r.w : r.y, kthr, thr, sbyte(oldw[0], 0));
+        const int s = pbit_next(wr, wu, kthr, thr, sbyte(oldw[0], 0));
         neww[0] = (uint32_t)(uint8_t)(int8_t)s;
     } else {
 #pragma unroll
-        for (int k = 0; k < G; k += 2) {
-            const uint4 r = philox((uint32_t)i, q, a.instance, (uint32_t)(t0 + k) >> 1, a.seed_lo, a.seed_hi);
-            const uint32_t k0 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k]));
-            const uint32_t k1 = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k + 1]));
-            const int s0 = pbit_next(r.x, r.y, k0, thr, sbyte(oldw[k >> 2], k & 3));
-            const int s1 = pbit_next(r.z, r.w, k1, thr, sbyte(oldw[k >> 2], (k & 3) + 1));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s0) << (8 * (k & 3));
-            neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s1) << (8 * ((k & 3) + 1));
+        for (int k = 0; k < G; k += 4) {
+            uint32_t wr[4], wu[4];
+            pbit_draws4((uint32_t)i, q, a.instance, (uint32_t)(t0 + k), a.seed_lo, a.seed_hi, wr, wu);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t kt = pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[k + b]));
+                const int s = pbit_next(wr[b], wu[b], kt, thr, sbyte(oldw[k >> 2], b));
+                neww[k >> 2] |= ((uint32_t)(uint8_t)(int8_t)s) << (8 * b);
+            }
         }
     }
     store_group<G>(a.out + (size_t)i * a.T + t0, neww);
@@ -597,9 +611,8 @@ __device__ __forceinline__ void variant_words(const StepArgs& a, int i, int tb, 
             for (int b = 0; b < 4; ++b) I[b] = __fmul_rn(I0, (float)D[4 * k + b]);
         }
         // decisions (Eq. 6): candidate +1 iff r-word k-value < kthr, update iff u-word < thr
-        uint4 r0, r1;
-        philox_pair((uint32_t)i, q, a.instance, (uint32_t)t >> 1, (uint32_t)(t + 2) >> 1, a.seed_lo, a.seed_hi, r0,
-                    r1);
+        uint32_t wr[4], wu[4];
+        pbit_draws4((uint32_t)i, q, a.instance, (uint32_t)t, a.seed_lo, a.seed_hi, wr, wu);
         uint32_t nk[4];
         if (table) {
 #pragma unroll
@@ -608,8 +621,8 @@ __device__ __forceinline__ void variant_words(const StepArgs& a, int i, int tb, 
 #pragma unroll
             for (int b = 0; b < 4; ++b) nk[b] = 0u - pbit_kthr_of_x(variant_x(a.offset_mode, I0, lam, del, I[b]));
         }
-        const uint32_t S = sign_bytes((r0.x >> 8) + nk[0], (r0.z >> 8) + nk[1], (r1.x >> 8) + nk[2], (r1.z >> 8) + nk[3]);
-        const uint32_t U = sign_bytes((r0.y >> 8) - thr, (r0.w >> 8) - thr, (r1.y >> 8) - thr, (r1.w >> 8) - thr);
+        const uint32_t S = sign_bytes((wr[0] >> 8) + nk[0], (wr[1] >> 8) + nk[1], (wr[2] >> 8) + nk[2], (wr[3] >> 8) + nk[3]);
+        const uint32_t U = sign_bytes((wu[0] >> 8) - thr, (wu[1] >> 8) - thr, (wu[2] >> 8) - thr, (wu[3] >> 8) - thr);
         const uint32_t old = wld32(src + cell);
         wst32(dst + cell, ((U & ~S) | (~U & old)) | 0x01010101u);
     }

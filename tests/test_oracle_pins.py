@@ -88,6 +88,61 @@ def test_draw_grids():
     assert abs(np.corrcoef(rs, us)[0, 1]) < 0.15
 
 
+def _draw_indices(seed, instance, node, step, trials):
+    """The integer grid indices (k of r, q of u) of the oracle's draws."""
+    k, q = [], []
+    for t in trials:
+        r, u = oracle.draw_ru(seed, instance, node, step, t)
+        k.append(int(round((r * 2**24 + 2**24 - 1) / 2)))
+        q.append(int(round(u * 2**24)))
+    return k, q
+
+
+def test_draw_layout_against_triton_philox():
+    """Every trial's r and u indices, pinned to Triton's independent Philox through the stated layout:
+    trials 8g .. 8g+7 share the blocks with last counter words 3g, 3g+1, 3g+2; trial k takes the top 24
+    bits of word k % 4 of block 3g + k // 4 as r, and as u the half k % 2 of word k // 2 of block 3g + 2
+    (high 16 bits) followed by the low byte of its r-word."""
+    pytest.importorskip("triton")
+    seed, instance, step = 0x0BAD_F00D_1234, 3, 77
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    nodes, trials = (0, 5, 300), list(range(20))
+    cases = [([i, step, instance, c], key) for i in nodes for c in range(9)]
+    script = os.path.join(ROOT, "tests", "golden", "triton_philox.py")
+    res = subprocess.run([sys.executable, script], input=json.dumps(cases), capture_output=True, text=True,
+                         env=dict(os.environ, TRITON_INTERPRET="1"), timeout=600)
+    if res.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {res.stderr[-300:]}")
+    words = json.loads(res.stdout)
+    for a, i in enumerate(nodes):
+        blocks = words[9 * a: 9 * a + 9]
+        k, q = _draw_indices(seed, instance, i, step, trials)
+        for t in trials:
+            g, kk = divmod(t, 8)
+            wr = blocks[3 * g + kk // 4][kk % 4]
+            half = (blocks[3 * g + 2][kk // 2] >> (16 * (kk % 2))) & 0xFFFF
+            assert k[t] == wr >> 8, (i, t)
+            assert q[t] == (half << 8) | (wr & 0xFF), (i, t)
+
+
+def test_draws_use_no_bit_twice():
+    """The 16 values a group of 8 trials draws (r and u of each, 24 bits each) take 384 distinct
+    Philox bits: over many (node, step) every pair of those bits agrees about half the time, and each
+    bit is balanced.  A bit shared by two values (a layout mistake) would agree every time."""
+    N = 6000
+    vals = np.empty((N, 16), np.int64)
+    for s in range(N):
+        k, q = _draw_indices(99, 1, s % 300, s // 300, range(8, 16))
+        vals[s, :8], vals[s, 8:] = k, q
+    bits = ((vals[:, :, None] >> np.arange(24)) & 1).reshape(N, 384).astype(np.float64)
+    sd = 0.5 / np.sqrt(N)
+    assert np.all(np.abs(bits.mean(axis=0) - 0.5) < 6 * sd)
+    x = 2 * bits - 1
+    agree = (x.T @ x) / N  # 2 P(equal) - 1
+    np.fill_diagonal(agree, 0.0)
+    assert np.abs(agree).max() < 12 * sd
+
+
 # ------------------------------------------------------------- MAX-CUT ------
 
 @pytest.mark.parametrize("n", [3, 4, 7, 10])
@@ -398,17 +453,18 @@ def test_init_spins_rule_against_triton_philox():
     pytest.importorskip("triton")
     seed, instance = 0x1234_5678_9ABC, 5
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    pairs = [(i, t) for i in (0, 1, 7, 40) for t in range(6)]
-    cases = [([i, 0xFFFFFFFF, instance, t >> 1], key) for i, t in pairs]
+    pairs = [(i, t) for i in (0, 1, 7, 40) for t in range(19)]
+    # trial t's r-word: output word t % 4 of the block with last counter word 3 (t // 8) + (t % 8) // 4
+    cases = [([i, 0xFFFFFFFF, instance, 3 * (t // 8) + (t % 8) // 4], key) for i, t in pairs]
     script = os.path.join(ROOT, "tests", "golden", "triton_philox.py")
     res = subprocess.run([sys.executable, script], input=json.dumps(cases), capture_output=True, text=True,
                          env=dict(os.environ, TRITON_INTERPRET="1"), timeout=600)
     if res.returncode != 0:
         pytest.skip(f"triton interpreter unavailable: {res.stderr[-300:]}")
     words = json.loads(res.stdout)
-    s = oracle.init_spins(41, 6, seed, instance)
+    s = oracle.init_spins(41, 19, seed, instance)
     for (i, t), w in zip(pairs, words):
-        want = 1 if (w[2 * (t & 1)] >> 31) == 0 else -1
+        want = 1 if (w[t % 4] >> 31) == 0 else -1
         assert s[i, t] == want, (i, t)
 
 

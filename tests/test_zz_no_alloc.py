@@ -1,9 +1,11 @@
 """pbit_anneal_noalloc: the allocation-free variant of pbit_anneal.
 
-It serves callers that cannot allocate device memory while they run (code in
-stream callbacks or host functions, applications whose allocator has
-reserved nearly all of HBM, latency-bound loops).  Its scratch is a fixed
-32 MiB array inside libpbit.so.  This file is named to be collected last, so
+It serves callers that cannot allocate device memory while they run:
+applications whose own caching allocator has reserved nearly all of HBM,
+processes under a fixed device-memory cap, and latency-bound loops that
+cannot absorb an allocation's synchronisation.  (It still calls the CUDA
+runtime, so it is not for stream callbacks or host functions.)  Its scratch
+is a fixed 32 MiB array inside libpbit.so.  This file is named to be collected last, so
 that a run stopping at its first failure has already run every other test;
 it also passes alone in a fresh process.
 """
