@@ -39,25 +39,25 @@ L2_FLUSH_BYTES = 512 << 20
 # the kernel's sources hash to the recorded value; otherwise the bench reports traffic null.
 TRAFFIC = {
     # one persistent launch: K_2000 +-1, 256 trials, 2000 steps, e4m3 kernel (forced; weights outside e2m1)
-    "dense_persistent_kernel": {"bytes": 4974336 + 391936, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "e04d2dc2027a0342"},
+    "dense_persistent_kernel": {"bytes": 4828928 + 403456, "files": ["pbit_dense.cu", "pbit_device.cuh"],
+                                "sha": "fa700aaaed1a46e8"},
     # one cluster-resident FP4 launch: K_2000 +-1, 256 trials, 2000 steps
-    "dense4_cluster_kernel": {"bytes": 2989312 + 0, "files": ["pbit_dense4.cu", "pbit_device.cuh"],
-                              "sha": "9531f8b17a5f31c5"},
+    "dense4_cluster_kernel": {"bytes": 3026944 + 0, "files": ["pbit_dense4.cu", "pbit_device.cuh"],
+                              "sha": "3e938333c60e6fae"},
     # one multi-step launch: 100x200 torus, 1024 trials, 5000 steps
-    "sparse_flow_kernel": {"bytes": 23502592 + 69804288,
+    "sparse_flow_kernel": {"bytes": 25699840 + 608477696,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
-                           "sha": "c116ca22e431f323"},
+                           "sha": "c2b5d9ae713109e4"},
     # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
-    "sparse_variant_words_kernel:spsa": {"bytes": 103563178 + 41197141,
+    "sparse_variant_words_kernel:spsa": {"bytes": 103571456 + 41346304,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "151f58073eddfe83"},
-    "sparse_variant_words_kernel:tapsa": {"bytes": 144534613 + 35485696,
+                                         "sha": "8f285e3ba2a1e113"},
+    "sparse_variant_words_kernel:tapsa": {"bytes": 144523264 + 35471531,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "151f58073eddfe83"},
+                                          "sha": "8f285e3ba2a1e113"},
     # per launch of a 64-step chunk of all 64 instances of the uneven batch
-    "batch_chunk_kernel": {"bytes": 1354917888 + 2004216064, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
-                           "sha": "9249f5b4ba245cc7", "chunk_steps": 64},
+    "batch_chunk_kernel": {"bytes": 1474757376 + 2120900608, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
+                           "sha": "143f66fe3fc6e55f", "chunk_steps": 64},
 }
 
 

@@ -406,6 +406,7 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 constexpr int kEpi = 512;                      // epilogue threads
 constexpr int kPersistThreads = kEpi + 32;
 constexpr int kMaxItems = 4;                   // (NT/2/KS) pairs x 32 row quads <= 4 x 512
+static_assert(kEpi == 4 * kRows, "the first kEpi items hold 4 groups of 4 trial pairs over kRows rows");
 
 // 17 warps share 4 SM sub-partitions (one holds 5 warps and 16K registers),
 // so the compiler keeps this kernel near 100 registers per thread.
@@ -534,16 +535,32 @@ __global__ void __launch_bounds__(kPersistThreads, 1) dense_persistent_kernel(Pe
                 }
             }
             __syncwarp();  // reconverge before the warp-aligned CTA barrier
-        } else if (tid < items) {
-            // this thread's Philox words for the step, drawn while the control warp waits
-            const int p = pb + (tid >> 5);
-            const int t0 = tb * NT + 2 * p;
-            const int i0 = rb * kRows + (tid & 31) * 4;
+        } else {
+            // the Philox words of the first kEpi items for the step, drawn while the control warp
+            // waits.  Where their pairs form whole groups of 8 trials, thread (group gl, row r) draws
+            // the group's three blocks for row r and hands each pair's words to the thread that
+            // decides it (3 blocks per 4 pairs and row instead of 2 per pair)
+            const int np0 = min(pe - pb, kEpi / 32);  // pairs of the first kEpi items
+            if (((tb * NT + 2 * pb) & 7) == 0 && (np0 & 3) == 0) {
+                const int gl = tid / kRows, r = tid % kRows;  // kEpi / kRows = 4 groups of 4 pairs
+                if (4 * gl < np0) {
+                    const uint32_t i = (uint32_t)(rb * kRows + r);
+                    const PhiloxHead ph = philox_head(i, (uint32_t)step, a.instance, a.seed_lo, a.seed_hi);
+                    const PbitPairs8 d =
+                        pbit_pairs8(ph, (uint32_t)(tb * NT + 2 * (pb + 4 * gl)), a.seed_lo, a.seed_hi);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                s_rw[k * kEpi + tid] = pbit_draws2((uint32_t)(i0 + k), (uint32_t)step, a.instance, (uint32_t)t0,
-                                                   a.seed_lo, a.seed_hi);
-            if (ls == 0) {
+                    for (int q = 0; q < 4; ++q) s_rw[(r & 3) * kEpi + (4 * gl + q) * 32 + (r >> 2)] = d.p[q];
+                }
+            } else if (tid < items) {
+                const int p = pb + (tid >> 5);
+                const int t0 = tb * NT + 2 * p;
+                const int i0 = rb * kRows + (tid & 31) * 4;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    s_rw[k * kEpi + tid] = pbit_draws2((uint32_t)(i0 + k), (uint32_t)step, a.instance,
+                                                       (uint32_t)t0, a.seed_lo, a.seed_hi);
+            }
+            if (tid < items && ls == 0) {
 #pragma unroll
                 for (int slot = 0; slot < kMaxItems; ++slot) {
                     const int it = tid + slot * kEpi;

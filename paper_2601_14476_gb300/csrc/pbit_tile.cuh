@@ -344,23 +344,19 @@ __device__ __forceinline__ void process_warp_items(const StepArgs& a, uint32_t t
     const PhiloxHead ph = philox_head((uint32_t)i, (uint32_t)a.step, a.instance, a.seed_lo, a.seed_hi);
 #pragma unroll
     for (int gq = 0; gq < NW / 2; ++gq) {
-        // one group of 8 trials (two words) from three Philox blocks: the u-halves of both words
-        // first, then each word's r-block
-        const uint32_t g3 = 3u * ((uint32_t)(t0 + 8 * gq) >> 3);
-        const uint4 b2 = philox_tail(ph, g3 + 2u, a.seed_lo, a.seed_hi);
+        // one group of 8 trials (two words) from three Philox blocks
+        const PbitPairs8 d = pbit_pairs8(ph, (uint32_t)(t0 + 8 * gq), a.seed_lo, a.seed_hi);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int w = 2 * gq + h;
-            const uint4 r = philox_tail(ph, g3 + (uint32_t)h, a.seed_lo, a.seed_hi);
-            const uint32_t s0 = h ? b2.z : b2.x, s1 = h ? b2.w : b2.y;
+            const uint4 p0 = d.p[2 * h], p1 = d.p[2 * h + 1];
             const uint32_t cnt = HALF ? cnt2[w] >> 1 : cnt2[w];  // bytes of cnt2 are even: halving keeps them apart
             // the shuffle width L keeps the source lane inside this node's segment
             uint32_t q[4];
 #pragma unroll
             for (int b = 0; b < 4; ++b) q[b] = __shfl_sync(0xFFFFFFFFu, negk_lane, (int)byte_of(cnt, b), L);
-            const uint32_t S = sign_bytes((r.x >> 8) + q[0], (r.y >> 8) + q[1], (r.z >> 8) + q[2], (r.w >> 8) + q[3]);
-            const uint32_t U = sign_bytes((pbit_uword(r.x, s0, false) >> 8) - thr, (pbit_uword(r.y, s0, true) >> 8) - thr,
-                                          (pbit_uword(r.z, s1, false) >> 8) - thr, (pbit_uword(r.w, s1, true) >> 8) - thr);
+            const uint32_t S = sign_bytes((p0.x >> 8) + q[0], (p0.z >> 8) + q[1], (p1.x >> 8) + q[2], (p1.z >> 8) + q[3]);
+            const uint32_t U = sign_bytes((p0.y >> 8) - thr, (p0.w >> 8) - thr, (p1.y >> 8) - thr, (p1.w >> 8) - thr);
             neww[w] = ((U & ~S) | (~U & oldw[w])) | 0x01010101u;
         }
     }

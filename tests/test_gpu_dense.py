@@ -91,8 +91,12 @@ def test_dense_operand_rejections():
     assert ei.value.code == pbit.PBIT_E_UNSUPPORTED
 
 
-@pytest.mark.parametrize("n,T", [(300, 64), (2000, 256)])
+@pytest.mark.parametrize("n,T", [(300, 64), (2000, 256), (2600, 32)])
 def test_dense_anneal_equals_sparse_anneal(n, T):
+    """The tensor-core kernel equals the sparse path step for step.  The CTAs of T = 64 and 256
+    decide whole groups of eight trials (three Philox blocks per group and row, handed to the pairs'
+    threads); at n = 2600, T = 32 the 16 trial pairs split over six K slices as 2 or 3 pairs per
+    CTA, starting at pairs 0, 2, 5, 8, 10, 13, so every CTA draws per pair instead."""
     g = _complete(n, 7)
     var = inputs.variability(n, 7, s_intensity=0.3, s_offset=0.3)
     G = pbit.Graph.from_inputs(g, dense=True)
