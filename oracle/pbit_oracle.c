@@ -49,7 +49,9 @@
  * quadratic-form cut identity for both orientations, cut = (W - H)/2 with
  * h = 0, I0 = 0 gives Bernoulli(1/2) decisions, I0 -> inf gives sgn of the
  * field, fields equal an int64 dense matmul, Philox equals Triton's
- * independent implementation, the schedule closed form.
+ * independent implementation (and so do every trial's r and u indices taken
+ * through the layout above), the 16 draws of a group share no bit, the
+ * schedule closed form.
  */
 #include <math.h>
 #include <stdint.h>
