@@ -40,24 +40,24 @@ L2_FLUSH_BYTES = 512 << 20
 TRAFFIC = {
     # one persistent launch: K_2000 +-1, 256 trials, 2000 steps, e4m3 kernel (forced; weights outside e2m1)
     "dense_persistent_kernel": {"bytes": 4828928 + 403456, "files": ["pbit_dense.cu", "pbit_device.cuh"],
-                                "sha": "fa700aaaed1a46e8"},
+                                "sha": "89e83f860105013d"},
     # one cluster-resident FP4 launch: K_2000 +-1, 256 trials, 2000 steps
     "dense4_cluster_kernel": {"bytes": 3026944 + 0, "files": ["pbit_dense4.cu", "pbit_device.cuh"],
-                              "sha": "3e938333c60e6fae"},
+                              "sha": "c0bd8b766236d721"},
     # one multi-step launch: 100x200 torus, 1024 trials, 5000 steps
     "sparse_flow_kernel": {"bytes": 25699840 + 608477696,
                            "files": ["pbit_tile.cuh", "pbit_flow.cu", "pbit_device.cuh"],
-                           "sha": "c2b5d9ae713109e4"},
+                           "sha": "44d9ecba49512c4c"},
     # per one-step launch of SpSA / TApSA (window 4) on the 100x200 torus, T = 1024
     "sparse_variant_words_kernel:spsa": {"bytes": 103571456 + 41346304,
                                          "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                         "sha": "8f285e3ba2a1e113"},
+                                         "sha": "96ab07d6c8cac8ed"},
     "sparse_variant_words_kernel:tapsa": {"bytes": 144523264 + 35471531,
                                           "files": ["pbit_variant.cu", "pbit_tile.cuh", "pbit_device.cuh"],
-                                          "sha": "8f285e3ba2a1e113"},
+                                          "sha": "96ab07d6c8cac8ed"},
     # per launch of a 64-step chunk of all 64 instances of the uneven batch
     "batch_chunk_kernel": {"bytes": 1474757376 + 2120900608, "files": ["pbit_tile.cuh", "pbit_batch.cu", "pbit_device.cuh"],
-                           "sha": "143f66fe3fc6e55f", "chunk_steps": 64},
+                           "sha": "189392b7e0472f25", "chunk_steps": 64},
 }
 
 

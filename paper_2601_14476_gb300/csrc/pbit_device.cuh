@@ -32,7 +32,8 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
 // Two Philox4x32-10 blocks whose counters differ only in the last word,
 // evaluated side by side (independent instruction streams for the scheduler).
 // The counters of this library put the per-trial word last: (node, step,
-// instance, trial pair).  The first round's two products and the second
+// instance, block index within the node's trial groups).  The first round's
+// two products and the second
 // round's first product then do not depend on the trial, so a thread that
 // draws for many trials of one node shares them (16 rather than 19 wide
 // multiplies per block once inlined).
@@ -65,8 +66,8 @@ __device__ __forceinline__ void philox_pair(uint32_t c0, uint32_t c1, uint32_t c
 // Philox4x32-10 split at the last counter word.  For counters (c0, c1, c2, c3)
 // the first round's two products, and the second round's product of the
 // first word, do not depend on c3; PhiloxHead keeps what the rest of the
-// rounds need of them, so a thread drawing for many values of c3 (the trial
-// pairs of one node) computes them once and each block then costs 16 wide
+// rounds need of them, so a thread drawing for many values of c3 (the blocks
+// of one node's trial groups) computes them once and each block then costs 16 wide
 // multiplies.  philox_tail(philox_head(c0, c1, c2, k), c3, k) equals
 // philox(c0, c1, c2, c3, k).
 struct PhiloxHead {
