@@ -1,5 +1,10 @@
 """Pins of the oracle's pSA variants (Eq. SpSA, Eq. TApSA) and the period
 timing model (T_res sub-steps per cycle) to special cases and closed forms."""
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -118,3 +123,32 @@ def test_spsa_stall_rate_and_full_stall():
     assert np.all(st.Iprev == 0)
     tot = 4 * out.size
     assert abs(ups / tot - 0.5) < 5 * 0.5 / np.sqrt(tot)
+
+
+def test_spsa_stall_draw_against_triton_philox():
+    """The SpSA stall draw (reading: word t mod 4 of Philox at counter (node, q, instance xor 2^31,
+    t / 4), stall iff its top 24 bits / 2^24 < p) pinned to Triton's independent Philox.  A stalled
+    (node, trial) keeps its previous input, so with every previous input set to NaN the NaNs left
+    after one sub-step mark exactly the stalls; at p = 1/2 a stall is a word whose top bit is 0."""
+    pytest.importorskip("triton")
+    g, csr, s, _ = _setup(n=5, m=8, T=12)
+    seed, instance, q = 0x7777_0000_1234, 6, 3
+    tab = oracle.schedule(csr, 0.1, 10.0, 8)
+    st = oracle.VariantState(g.n, 12)
+    st.Iprev[:] = np.nan
+    oracle.step_variant(csr, s, q, tab, seed, instance, algorithm=oracle.ALG_SPSA, stall_prob=0.5, state=st)
+    stalled = np.isnan(st.Iprev)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    cases = [([i, q, instance ^ 0x80000000, c], key) for i in range(g.n) for c in range(3)]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = os.path.join(root, "tests", "golden", "triton_philox.py")
+    res = subprocess.run([sys.executable, script], input=json.dumps(cases), capture_output=True, text=True,
+                         env=dict(os.environ, TRITON_INTERPRET="1"), timeout=600)
+    if res.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {res.stderr[-300:]}")
+    words = json.loads(res.stdout)
+    for i in range(g.n):
+        for t in range(12):
+            w = words[3 * i + t // 4][t % 4]
+            assert stalled[i, t] == ((w >> 31) == 0), (i, t)
+    assert 0 < stalled.sum() < stalled.size
