@@ -165,7 +165,9 @@ typedef struct {
     int32_t i0_normalize;    /* 1: divide the end points by mean_s (the paper's rule) */
     int32_t offset_mode;     /* pbit_offset_mode */
     uint64_t seed;           /* Philox key */
-    uint32_t instance;       /* Philox counter word 3 */
+    uint32_t instance;       /* the third Philox counter word (node, step, instance, c); SpSA's
+                                stall draws use instance ^ 0x80000000, so keep instance < 2^31
+                                where SpSA runs beside another instance's pSA draws */
     int32_t kernel;          /* pbit_kernel */
     const float* intensity;  /* HOST float[n] lambda_i, NULL = 1 */
     const float* offset;     /* HOST float[n] delta_i, NULL = 0 */
